@@ -1,0 +1,200 @@
+"""CPU oracle for exhaustive finite Kripke evaluation -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+legs may import this package.  The product path (``paper_2606_15437_gb300``)
+never imports it, and it imports nothing from the product: the two share no
+code.  The arithmetic lives in ``oracle.c`` (a recursive truth-set evaluator
+over explicit relations, the satisfaction clauses of Sec. 2 written out);
+this module only compiles it with gcc and marshals arguments.
+
+``pyref`` holds an even simpler pure-Python path (sets of pairs, per-world
+recursion) used to pin ``oracle.c`` by brute force on tiny inputs.
+"""
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+CLASSES = ("K", "T", "S4", "S5")
+
+
+def build(force=False):
+    """Compile oracle.c into _build/liboracle.so (plain gcc, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    tmp = _SO + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+                           "-o", tmp, _SRC])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _Census(ctypes.Structure):
+    _fields_ = [("frames", ctypes.c_uint64), ("cm_count", ctypes.c_uint64),
+                ("frames_refuted", ctypes.c_uint64), ("found", ctypes.c_int32),
+                ("nvals", ctypes.c_int32), ("wf", ctypes.c_uint64),
+                ("wv", ctypes.c_uint32), ("ww", ctypes.c_uint32)]
+
+
+class _Pair(ctypes.Structure):
+    _fields_ = [("found", ctypes.c_int32), ("nvals", ctypes.c_int32),
+                ("f", ctypes.c_uint64), ("v", ctypes.c_uint32), ("w", ctypes.c_uint32),
+                ("phi_val", ctypes.c_int32), ("psi_val", ctypes.c_int32),
+                ("frames_disagree", ctypes.c_uint64)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            u64, u32, i32, p = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_void_p
+            cs = ctypes.c_char_p
+            lib.orc_census.argtypes = [cs, i32, i32, u32, p, u64, u64, ctypes.POINTER(_Census)]
+            lib.orc_pair_layer.argtypes = [cs, cs, i32, u32, p, u64, u64, ctypes.POINTER(_Pair)]
+            lib.orc_pair_sampled.argtypes = [cs, cs, i32, u64, u32, p, u64, u64, ctypes.POINTER(_Pair)]
+            lib.orc_eval_model.argtypes = [cs, i32, p, p, p]
+            lib.orc_in_class.argtypes = [i32, i32, p]
+            lib.orc_class_size.argtypes = [i32, i32]
+            lib.orc_class_size.restype = u64
+            lib.orc_sample_frame.argtypes = [u64, i32, u64]
+            lib.orc_sample_frame.restype = u64
+            lib.orc_splitmix_out.argtypes = [u64, u64]
+            lib.orc_splitmix_out.restype = u64
+            lib.orc_stream_state.argtypes = [u64, u64, u64]
+            lib.orc_stream_state.restype = u64
+            lib.orc_frame_valid_all.argtypes = [cs, i32, p]
+            lib.orc_nvars.argtypes = [cs]
+            lib.orc_nodes.argtypes = [cs]
+            _lib = lib
+    return _lib
+
+
+def _cls(c):
+    return CLASSES.index(c) if isinstance(c, str) else int(c)
+
+
+def _samples(samples):
+    if samples is None:
+        return None, 0, None
+    a = np.ascontiguousarray(np.asarray(samples, dtype=np.uint32))
+    return a, len(a), a.ctypes.data_as(ctypes.c_void_p)
+
+
+def census(text, cls, n, samples=None, f_lo=0, f_hi=2 ** 64 - 1):
+    """Census of one formula on one (class, n) layer, frames with K index in
+    [f_lo, f_hi).  ``samples`` = the layer's sampled valuations (None: always
+    exhaustive).  Returns a dict; ``witness`` is (frame, valuation, world)."""
+    lib = _load()
+    keep, S, ptr = _samples(samples)
+    out = _Census()
+    rc = lib.orc_census(text.encode(), _cls(cls), n, S, ptr, f_lo, f_hi, ctypes.byref(out))
+    if rc:
+        raise ValueError("oracle census failed (%d) for %r" % (rc, text))
+    return {"frames": out.frames, "cm_count": out.cm_count,
+            "frames_refuted": out.frames_refuted, "nvals": out.nvals,
+            "witness": (out.wf, out.wv, out.ww) if out.found else None}
+
+
+def _pair_dict(out):
+    return {"nvals": out.nvals, "frames_disagree": out.frames_disagree,
+            "split": (out.f, out.v, out.w, out.phi_val, out.psi_val) if out.found else None}
+
+
+def pair_layer(phi, psi, n, samples=None, f_lo=0, f_hi=2 ** 64 - 1):
+    """First (frame, valuation, world) where phi and psi differ on n worlds."""
+    lib = _load()
+    keep, S, ptr = _samples(samples)
+    out = _Pair()
+    rc = lib.orc_pair_layer(phi.encode(), psi.encode(), n, S, ptr, f_lo, f_hi, ctypes.byref(out))
+    if rc:
+        raise ValueError("oracle pair_layer failed (%d)" % rc)
+    return _pair_dict(out)
+
+
+def pair_sampled(phi, psi, n, seed, s_lo, s_hi, samples=None):
+    """First disagreement on the sampled n-world relations s in [s_lo, s_hi)."""
+    lib = _load()
+    keep, S, ptr = _samples(samples)
+    out = _Pair()
+    rc = lib.orc_pair_sampled(phi.encode(), psi.encode(), n, seed, S, ptr, s_lo, s_hi,
+                              ctypes.byref(out))
+    if rc:
+        raise ValueError("oracle pair_sampled failed (%d)" % rc)
+    return _pair_dict(out)
+
+
+def eval_model(text, R, V=None):
+    """Truth value at every world of the explicit model: R is an n x n 0/1
+    matrix, V a (vars x n) 0/1 matrix."""
+    lib = _load()
+    R = np.ascontiguousarray(np.asarray(R, dtype=np.uint8))
+    n = R.shape[0]
+    if V is None:
+        V = np.zeros((8, n), np.uint8)
+    V = np.ascontiguousarray(np.asarray(V, dtype=np.uint8))
+    if V.shape[0] < 8:
+        V = np.ascontiguousarray(np.vstack([V, np.zeros((8 - V.shape[0], n), np.uint8)]))
+    out = np.zeros(n, np.uint8)
+    rc = lib.orc_eval_model(text.encode(), n, R.ctypes.data_as(ctypes.c_void_p),
+                            V.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p))
+    if rc:
+        raise ValueError("oracle eval_model failed (%d)" % rc)
+    return out
+
+
+def frame_valid_all(text, n):
+    """uint8[2^(n*n)]: 1 where the K-indexed frame validates ``text``."""
+    lib = _load()
+    out = np.zeros(1 << (n * n), np.uint8)
+    rc = lib.orc_frame_valid_all(text.encode(), n, out.ctypes.data_as(ctypes.c_void_p))
+    if rc:
+        raise ValueError("oracle frame_valid_all failed (%d)" % rc)
+    return out
+
+
+def in_class(cls, R):
+    lib = _load()
+    R = np.ascontiguousarray(np.asarray(R, dtype=np.uint8))
+    return bool(lib.orc_in_class(_cls(cls), R.shape[0], R.ctypes.data_as(ctypes.c_void_p)))
+
+
+def class_size(cls, n):
+    return int(_load().orc_class_size(_cls(cls), n))
+
+
+def sample_frame(seed, n, s):
+    """Row-major edge mask of sampled n-world relation number s."""
+    return int(_load().orc_sample_frame(seed, n, s))
+
+
+def splitmix_out(state, j):
+    return int(_load().orc_splitmix_out(state, j))
+
+
+def stream_state(seed, tag, n):
+    return int(_load().orc_stream_state(seed, tag, n))
+
+
+def nvars(text):
+    return int(_load().orc_nvars(text.encode()))
+
+
+def frame_matrix(f, n):
+    """The n x n relation of K index f (R(w,v) = bit w*n+v)."""
+    return np.array([[(f >> (w * n + v)) & 1 for v in range(n)] for w in range(n)], np.uint8)
+
+
+def threads():
+    return int(_load().orc_threads())

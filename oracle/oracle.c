@@ -1,0 +1,487 @@
+/*
+ * oracle.c -- plain, slow CPU oracle for exhaustive finite Kripke evaluation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link or call
+ * this file: only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline
+ * leg (and bench.py --impl reference) use it.  It shares no code, header,
+ * table or helper with the CUDA path.
+ *
+ * Everything here is the textbook definition written out, over explicit
+ * relations (uint8 R[w*n+v]) and explicit valuations (uint8 V[i*n+w]):
+ *
+ *   formulas      phi ::= T | F | p_i | ~phi | phi&phi | phi|phi | phi->phi
+ *                         | []phi | <>phi                     (Sec. 2)
+ *                 (phi<->psi is accepted as sugar for the biconditional of
+ *                  Prop. 6.)
+ *   satisfaction  w |= []phi iff for all v, R(w,v) implies v |= phi;
+ *                 w |= <>phi iff some v has R(w,v) and v |= phi   (Sec. 2)
+ *   classes       K all frames, T reflexive, S4 reflexive+transitive,
+ *                 S5 reflexive+transitive+symmetric             (Sec. 2)
+ *   countermodel  (F, V, w) with M,w not|= phi                  (Sec. 2)
+ *   census        per (formula, class, n): the number of refuted
+ *                 (frame, valuation) pairs, the number of refuted frames,
+ *                 and the lexicographically least (frame, valuation, world)
+ *                 witness -- the outputs of the corpus scan of Alg. 1 (Sec. 4)
+ *   separation    the least (n, frame, valuation, world) at which phi and
+ *                 psi take different truth values (Def. 2, Prop. 6, Sec. 7)
+ *
+ * Readings of the paper where it is silent (each is listed in the design doc):
+ *   - frame index f of an n-world frame: R(w,v) is bit (w*n+v) of f
+ *     (so successor mask succ[w] is bits [w*n, w*n+n) of f);
+ *   - valuation index x: p_i holds at w iff bit (i*n+w) of x is set;
+ *   - k = 1 + the highest variable index occurring (0 if none);
+ *   - valuations are exhaustive (x = 0 .. 2^(k n)-1) when S == 0, k <= 1 or
+ *     2^(k n) <= S; otherwise the S sampled values samp[j] (low k n bits) are
+ *     used in slot order j, counted with multiplicity;
+ *   - the witness valuation index is x for exhaustive valuations and the slot
+ *     j for sampled ones;
+ *   - sampled 7/8-world frames come from SplitMix64 (Steele, Lea and Flood,
+ *     OOPSLA 2014) in its counter form, see orc_sample_frame().
+ *
+ * The evaluator computes each subformula's truth value at every world by the
+ * satisfaction clauses above (a bool per world, no bit tricks).  Frame loops
+ * run under OpenMP; every reduction is a sum or a lexicographic minimum, so
+ * the results do not depend on the thread count.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <ctype.h>
+#include <omp.h>
+
+#define ORC_MAX_NODES 256
+#define ORC_MAX_VARS 8
+#define ORC_MAX_WORLDS 32
+
+enum { O_TOP, O_BOT, O_VAR, O_NOT, O_AND, O_OR, O_IMP, O_IFF, O_BOX, O_DIA };
+
+typedef struct { int kind, var, a, b; } onode;
+typedef struct { onode nd[ORC_MAX_NODES]; int nn, root, nvars, err; } oform;
+
+/* ------------------------------------------------------------------ parser */
+
+typedef struct { const char *s; int i; oform *f; } opar;
+
+static void skip_ws(opar *p) { while (p->s[p->i] && isspace((unsigned char)p->s[p->i])) p->i++; }
+
+static int lit(opar *p, const char *t) {
+    skip_ws(p);
+    size_t L = strlen(t);
+    if (strncmp(p->s + p->i, t, L) != 0) return 0;
+    /* a keyword must not run into an identifier character */
+    if (isalpha((unsigned char)t[0]) && isalnum((unsigned char)p->s[p->i + L])) return 0;
+    p->i += (int)L;
+    return 1;
+}
+
+static int mk(opar *p, int kind, int var, int a, int b) {
+    oform *f = p->f;
+    if (f->nn >= ORC_MAX_NODES) { f->err = 1; return 0; }
+    f->nd[f->nn].kind = kind; f->nd[f->nn].var = var;
+    f->nd[f->nn].a = a; f->nd[f->nn].b = b;
+    return f->nn++;
+}
+
+static int p_iff(opar *p);
+
+static int p_unary(opar *p) {
+    if (p->f->err) return 0;
+    if (lit(p, "~") || lit(p, "!") || lit(p, "not")) return mk(p, O_NOT, 0, p_unary(p), -1);
+    if (lit(p, "[]") || lit(p, "box")) return mk(p, O_BOX, 0, p_unary(p), -1);
+    if (lit(p, "<>") || lit(p, "dia")) return mk(p, O_DIA, 0, p_unary(p), -1);
+    if (lit(p, "(")) {
+        int e = p_iff(p);
+        if (!lit(p, ")")) p->f->err = 1;
+        return e;
+    }
+    if (lit(p, "T") || lit(p, "true")) return mk(p, O_TOP, 0, -1, -1);
+    if (lit(p, "F") || lit(p, "false")) return mk(p, O_BOT, 0, -1, -1);
+    skip_ws(p);
+    char c = p->s[p->i];
+    if (c == 'p' || c == 'q' || c == 'r' || c == 's') {
+        int var;
+        p->i++;
+        if (c == 'p' && isdigit((unsigned char)p->s[p->i])) {
+            var = 0;
+            while (isdigit((unsigned char)p->s[p->i])) var = var * 10 + (p->s[p->i++] - '0');
+        } else {
+            var = (c == 'p') ? 0 : (c == 'q') ? 1 : (c == 'r') ? 2 : 3;
+        }
+        if (isalnum((unsigned char)p->s[p->i]) || var >= ORC_MAX_VARS) { p->f->err = 1; return 0; }
+        if (var + 1 > p->f->nvars) p->f->nvars = var + 1;
+        return mk(p, O_VAR, var, -1, -1);
+    }
+    p->f->err = 1;
+    return 0;
+}
+
+static int p_and(opar *p) {
+    int e = p_unary(p);
+    while (!p->f->err && (lit(p, "&") || lit(p, "and"))) e = mk(p, O_AND, 0, e, p_unary(p));
+    return e;
+}
+
+static int p_or(opar *p) {
+    int e = p_and(p);
+    while (!p->f->err && (lit(p, "|") || lit(p, "or"))) e = mk(p, O_OR, 0, e, p_and(p));
+    return e;
+}
+
+static int p_imp(opar *p) {                 /* right associative */
+    int e = p_or(p);
+    skip_ws(p);
+    if (!p->f->err && strncmp(p->s + p->i, "<->", 3) != 0 && lit(p, "->")) return mk(p, O_IMP, 0, e, p_imp(p));
+    return e;
+}
+
+static int p_iff(opar *p) {
+    int e = p_imp(p);
+    while (!p->f->err && lit(p, "<->")) e = mk(p, O_IFF, 0, e, p_imp(p));
+    return e;
+}
+
+static int parse(const char *text, oform *f) {
+    opar p = { text, 0, f };
+    memset(f, 0, sizeof(*f));
+    f->root = p_iff(&p);
+    skip_ws(&p);
+    if (p.s[p.i] != 0) f->err = 1;
+    return f->err ? -1 : 0;
+}
+
+/* ------------------------------------------------------ truth-set evaluator */
+
+/* out[w] = 1 iff M,w |= node, for every world w of the model (R, V) on n
+   worlds.  Each case is the satisfaction clause for that connective. */
+static void truth(const oform *f, int id, int n, const uint8_t *R, const uint8_t *V, uint8_t *out) {
+    const onode *x = &f->nd[id];
+    uint8_t a[ORC_MAX_WORLDS], b[ORC_MAX_WORLDS];
+    int w, v;
+    switch (x->kind) {
+    case O_TOP: for (w = 0; w < n; w++) out[w] = 1; return;
+    case O_BOT: for (w = 0; w < n; w++) out[w] = 0; return;
+    case O_VAR: for (w = 0; w < n; w++) out[w] = V[x->var * n + w]; return;
+    case O_NOT:
+        truth(f, x->a, n, R, V, a);
+        for (w = 0; w < n; w++) out[w] = !a[w];
+        return;
+    case O_AND: case O_OR: case O_IMP: case O_IFF:
+        truth(f, x->a, n, R, V, a);
+        truth(f, x->b, n, R, V, b);
+        for (w = 0; w < n; w++) {
+            if (x->kind == O_AND) out[w] = a[w] && b[w];
+            else if (x->kind == O_OR) out[w] = a[w] || b[w];
+            else if (x->kind == O_IMP) out[w] = !a[w] || b[w];
+            else out[w] = (a[w] == b[w]);
+        }
+        return;
+    case O_BOX:   /* every R-successor satisfies the argument */
+        truth(f, x->a, n, R, V, a);
+        for (w = 0; w < n; w++) {
+            out[w] = 1;
+            for (v = 0; v < n; v++) if (R[w * n + v] && !a[v]) out[w] = 0;
+        }
+        return;
+    case O_DIA:   /* some R-successor satisfies the argument */
+        truth(f, x->a, n, R, V, a);
+        for (w = 0; w < n; w++) {
+            out[w] = 0;
+            for (v = 0; v < n; v++) if (R[w * n + v] && a[v]) out[w] = 1;
+        }
+        return;
+    }
+}
+
+/* ---------------------------------------------------------- frame classes */
+
+static int reflexive(int n, const uint8_t *R) {
+    for (int w = 0; w < n; w++) if (!R[w * n + w]) return 0;
+    return 1;
+}
+static int transitive(int n, const uint8_t *R) {
+    for (int w = 0; w < n; w++) for (int v = 0; v < n; v++) for (int u = 0; u < n; u++)
+        if (R[w * n + v] && R[v * n + u] && !R[w * n + u]) return 0;
+    return 1;
+}
+static int symmetric(int n, const uint8_t *R) {
+    for (int w = 0; w < n; w++) for (int v = 0; v < n; v++)
+        if (R[w * n + v] && !R[v * n + w]) return 0;
+    return 1;
+}
+/* cls: 0 = K, 1 = T, 2 = S4, 3 = S5 */
+static int in_class(int cls, int n, const uint8_t *R) {
+    if (cls == 0) return 1;
+    if (!reflexive(n, R)) return 0;
+    if (cls == 1) return 1;
+    if (!transitive(n, R)) return 0;
+    if (cls == 2) return 1;
+    return symmetric(n, R);
+}
+
+static void decode_frame(uint64_t f, int n, uint8_t *R) {
+    for (int e = 0; e < n * n; e++) R[e] = (uint8_t)((f >> e) & 1u);
+}
+static void decode_val(uint64_t x, int k, int n, uint8_t *V) {
+    for (int e = 0; e < k * n; e++) V[e] = (uint8_t)((x >> e) & 1u);
+}
+
+/* The valuation set of a layer (reading listed in the header). */
+static int exhaustive_vals(int k, int n, uint32_t S) {
+    if (S == 0 || k <= 1) return 1;
+    if (k * n >= 32) return 0;
+    return ((uint64_t)1 << (k * n)) <= S;
+}
+
+/* ------------------------------------------------------------- SplitMix64 */
+
+/* SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the generator adds the
+   golden-ratio increment to its state and returns the state passed through
+   the "mix13" finaliser.  The j-th output (j = 0, 1, ...) of a generator
+   started at state s is therefore mix(s + (j+1)*gamma). */
+#define SM_GAMMA 0x9E3779B97F4A7C15ULL
+static uint64_t sm_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+uint64_t orc_splitmix_out(uint64_t state, uint64_t j) { return sm_mix(state + (j + 1) * SM_GAMMA); }
+/* the state that starts stream `tag` at frame size n for seed `seed` */
+uint64_t orc_stream_state(uint64_t seed, uint64_t tag, uint64_t n) { return sm_mix(seed ^ (tag << 32) ^ n); }
+
+/* Sampled n-world relation number s (n <= 8) of the Erdos-Renyi family with a
+   per-sample edge probability in [0.1, 0.5] (Sec. 7, adversarial frames):
+   nine draws per sample from stream tag 2; draw 0 gives the threshold
+   t = 26 + floor(hi32(draw0) * 103 / 2^32) in [26, 128] (p = t/256); edge e
+   (row-major, e = w*n+v) is present iff byte (e mod 8) of draw 1 + e/8 is
+   below t.  Returns the relation as a row-major edge mask. */
+uint64_t orc_sample_frame(uint64_t seed, int n, uint64_t s) {
+    uint64_t st = orc_stream_state(seed, 2, (uint64_t)n);
+    uint64_t d0 = orc_splitmix_out(st, 9 * s);
+    uint64_t t = 26 + (((d0 >> 32) * 103ULL) >> 32);
+    uint64_t mask = 0;
+    for (int e = 0; e < n * n; e++) {
+        uint64_t d = orc_splitmix_out(st, 9 * s + 1 + (uint64_t)(e / 8));
+        uint64_t byte = (d >> (8 * (e % 8))) & 0xFFu;
+        if (byte < t) mask |= (uint64_t)1 << e;
+    }
+    return mask;
+}
+
+/* ---------------------------------------------------------------- census */
+
+typedef struct {
+    uint64_t frames;          /* class frames in the index range            */
+    uint64_t cm_count;        /* refuted (frame, valuation) pairs           */
+    uint64_t frames_refuted;  /* frames with at least one refuted valuation */
+    int32_t  found;
+    int32_t  nvals;           /* valuations per frame                       */
+    uint64_t wf;              /* witness frame (K index)                    */
+    uint32_t wv;              /* witness valuation (index or sample slot)   */
+    uint32_t ww;              /* witness world                              */
+} orc_census_out;
+
+int orc_nvars(const char *text) {
+    oform f;
+    if (parse(text, &f)) return -1;
+    return f.nvars;
+}
+
+int orc_nodes(const char *text) {
+    oform f;
+    if (parse(text, &f)) return -1;
+    return f.nn;
+}
+
+/* Census of one formula over the class-`cls` frames on n worlds whose K
+   index lies in [f_lo, f_hi). */
+int orc_census(const char *text, int cls, int n, uint32_t S, const uint32_t *samp,
+               uint64_t f_lo, uint64_t f_hi, orc_census_out *out) {
+    oform f;
+    memset(out, 0, sizeof(*out));
+    if (n < 1 || n > 6 || cls < 0 || cls > 3) return -2;
+    if (parse(text, &f)) return -1;
+    int k = f.nvars;
+    int exh = exhaustive_vals(k, n, S);
+    if (!exh && samp == NULL) return -3;
+    if (exh && k * n > 30) return -4;
+    uint64_t nval = exh ? ((uint64_t)1 << (k * n)) : S;
+    uint32_t vmask = (k * n >= 32) ? 0xFFFFFFFFu : (uint32_t)(((uint64_t)1 << (k * n)) - 1);
+    uint64_t nf = (uint64_t)1 << (n * n);
+    if (f_hi > nf) f_hi = nf;
+    out->nvals = (int32_t)nval;
+
+    uint64_t frames = 0, cm = 0, fr = 0;
+    uint64_t best_f = UINT64_MAX; uint32_t best_v = 0, best_w = 0;
+    #pragma omp parallel
+    {
+        uint64_t lf = UINT64_MAX; uint32_t lv = 0, lw = 0;
+        #pragma omp for schedule(dynamic, 1024) reduction(+:frames,cm,fr)
+        for (int64_t fi = (int64_t)f_lo; fi < (int64_t)f_hi; fi++) {
+            uint8_t R[64], V[ORC_MAX_VARS * 8], t[8];
+            decode_frame((uint64_t)fi, n, R);
+            if (!in_class(cls, n, R)) continue;
+            frames++;
+            int any = 0;
+            for (uint64_t j = 0; j < nval; j++) {
+                uint64_t x = exh ? j : (samp[j] & vmask);
+                decode_val(x, k, n, V);
+                truth(&f, f.root, n, R, V, t);
+                int w0 = -1;
+                for (int w = 0; w < n; w++) if (!t[w]) { w0 = w; break; }
+                if (w0 >= 0) {
+                    cm++;
+                    any = 1;
+                    if ((uint64_t)fi < lf) { lf = (uint64_t)fi; lv = (uint32_t)j; lw = (uint32_t)w0; }
+                }
+            }
+            fr += any;
+        }
+        #pragma omp critical
+        {
+            if (lf < best_f || (lf == best_f && (lv < best_v || (lv == best_v && lw < best_w)))) {
+                best_f = lf; best_v = lv; best_w = lw;
+            }
+        }
+    }
+    out->frames = frames; out->cm_count = cm; out->frames_refuted = fr;
+    if (best_f != UINT64_MAX) { out->found = 1; out->wf = best_f; out->wv = best_v; out->ww = best_w; }
+    return 0;
+}
+
+/* Number of class-`cls` frames on n worlds (brute force over all relations). */
+uint64_t orc_class_size(int cls, int n) {
+    uint64_t nf = (uint64_t)1 << (n * n), c = 0;
+    #pragma omp parallel for reduction(+:c) schedule(static)
+    for (int64_t fi = 0; fi < (int64_t)nf; fi++) {
+        uint8_t R[64];
+        decode_frame((uint64_t)fi, n, R);
+        c += (uint64_t)in_class(cls, n, R);
+    }
+    return c;
+}
+
+/* ------------------------------------------------------------- separation */
+
+typedef struct {
+    int32_t  found;
+    int32_t  nvals;
+    uint64_t f;                /* K index (exhaustive) or sample index     */
+    uint32_t v;                /* valuation index or sample slot           */
+    uint32_t w;                /* least world where the two values differ  */
+    int32_t  phi_val, psi_val; /* truth values of phi and psi at that world */
+    uint64_t frames_disagree;  /* frames (in range) with any disagreement  */
+} orc_pair_out;
+
+static int pair_scan(const oform *fa, const oform *fb, int n, uint32_t S, const uint32_t *samp,
+                     uint64_t lo, uint64_t hi, int sampled, uint64_t seed, orc_pair_out *out) {
+    int k = fa->nvars > fb->nvars ? fa->nvars : fb->nvars;
+    int exh = exhaustive_vals(k, n, S);
+    if (!exh && samp == NULL) return -3;
+    if (exh && k * n > 30) return -4;
+    uint64_t nval = exh ? ((uint64_t)1 << (k * n)) : S;
+    uint32_t vmask = (k * n >= 32) ? 0xFFFFFFFFu : (uint32_t)(((uint64_t)1 << (k * n)) - 1);
+    out->nvals = (int32_t)nval;
+    uint64_t best_f = UINT64_MAX; uint32_t best_v = 0, best_w = 0; int best_a = 0, best_b = 0;
+    uint64_t dis = 0;
+    #pragma omp parallel
+    {
+        uint64_t lf = UINT64_MAX; uint32_t lv = 0, lw = 0; int la = 0, lb = 0;
+        #pragma omp for schedule(dynamic, 1024) reduction(+:dis)
+        for (int64_t fi = (int64_t)lo; fi < (int64_t)hi; fi++) {
+            uint8_t R[64], V[ORC_MAX_VARS * 8], ta[8], tb[8];
+            uint64_t rel = sampled ? orc_sample_frame(seed, n, (uint64_t)fi) : (uint64_t)fi;
+            decode_frame(rel, n, R);
+            int any = 0;
+            for (uint64_t j = 0; j < nval; j++) {
+                uint64_t x = exh ? j : (samp[j] & vmask);
+                decode_val(x, k, n, V);
+                truth(fa, fa->root, n, R, V, ta);
+                truth(fb, fb->root, n, R, V, tb);
+                for (int w = 0; w < n; w++) {
+                    if (ta[w] != tb[w]) {
+                        any = 1;
+                        if ((uint64_t)fi < lf) { lf = (uint64_t)fi; lv = (uint32_t)j; lw = (uint32_t)w; la = ta[w]; lb = tb[w]; }
+                        break;
+                    }
+                }
+            }
+            dis += any;
+        }
+        #pragma omp critical
+        {
+            if (lf < best_f || (lf == best_f && (lv < best_v || (lv == best_v && lw < best_w)))) {
+                best_f = lf; best_v = lv; best_w = lw; best_a = la; best_b = lb;
+            }
+        }
+    }
+    out->frames_disagree = dis;
+    if (best_f != UINT64_MAX) {
+        out->found = 1; out->f = best_f; out->v = best_v; out->w = best_w;
+        out->phi_val = best_a; out->psi_val = best_b;
+    }
+    return 0;
+}
+
+/* First disagreement of phi and psi among the n-world frames with K index
+   in [f_lo, f_hi). */
+int orc_pair_layer(const char *phi, const char *psi, int n, uint32_t S, const uint32_t *samp,
+                   uint64_t f_lo, uint64_t f_hi, orc_pair_out *out) {
+    oform fa, fb;
+    memset(out, 0, sizeof(*out));
+    if (n < 1 || n > 6) return -2;
+    if (parse(phi, &fa) || parse(psi, &fb)) return -1;
+    uint64_t nf = (uint64_t)1 << (n * n);
+    if (f_hi > nf) f_hi = nf;
+    return pair_scan(&fa, &fb, n, S, samp, f_lo, f_hi, 0, 0, out);
+}
+
+/* First disagreement among sampled n-world relations s in [s_lo, s_hi). */
+int orc_pair_sampled(const char *phi, const char *psi, int n, uint64_t seed, uint32_t S,
+                     const uint32_t *samp, uint64_t s_lo, uint64_t s_hi, orc_pair_out *out) {
+    oform fa, fb;
+    memset(out, 0, sizeof(*out));
+    if (n < 1 || n > 8) return -2;
+    if (parse(phi, &fa) || parse(psi, &fb)) return -1;
+    return pair_scan(&fa, &fb, n, S, samp, s_lo, s_hi, 1, seed, out);
+}
+
+/* ----------------------------------------------------------- one model */
+
+/* Truth value of `text` at every world of the explicit model (R, V) on n
+   worlds (n <= 32); V holds nvars rows of n entries. */
+int orc_eval_model(const char *text, int n, const uint8_t *R, const uint8_t *V, uint8_t *out) {
+    oform f;
+    if (n < 1 || n > ORC_MAX_WORLDS) return -2;
+    if (parse(text, &f)) return -1;
+    truth(&f, f.root, n, R, V, out);
+    return 0;
+}
+
+/* valid[f] = 1 iff frame f (K index) on n worlds validates `text`: the
+   formula is true at every world under every valuation of its variables. */
+int orc_frame_valid_all(const char *text, int n, uint8_t *valid) {
+    oform f;
+    if (n < 1 || n > 5) return -2;
+    if (parse(text, &f)) return -1;
+    int k = f.nvars;
+    if (k * n > 24) return -4;
+    uint64_t nf = (uint64_t)1 << (n * n), nval = (uint64_t)1 << (k * n);
+    #pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t fi = 0; fi < (int64_t)nf; fi++) {
+        uint8_t R[64], V[ORC_MAX_VARS * 8], t[8];
+        decode_frame((uint64_t)fi, n, R);
+        int ok = 1;
+        for (uint64_t x = 0; x < nval && ok; x++) {
+            decode_val(x, k, n, V);
+            truth(&f, f.root, n, R, V, t);
+            for (int w = 0; w < n; w++) if (!t[w]) ok = 0;
+        }
+        valid[fi] = (uint8_t)ok;
+    }
+    return 0;
+}
+
+/* 1 iff the relation R on n worlds is in class cls. */
+int orc_in_class(int cls, int n, const uint8_t *R) { return in_class(cls, n, R); }
+
+int orc_threads(void) { return omp_get_max_threads(); }

@@ -1,0 +1,275 @@
+"""Seeded synthetic workloads shaped like the paper's.
+
+This module only makes inputs: formula texts, formula pairs and the tables of
+sampled valuations.  It holds none of the evaluation arithmetic, so both the
+CUDA path and the CPU oracle can take their inputs from it.
+
+Workloads (the recipe is restated in the design doc):
+
+* ``pr1_formulas``      -- 64 random formulas over p, q (length <= 12, modal
+  depth <= 3) plus the K, T and 4 axioms; census over n <= 3, all valuations.
+* ``census5_formulas``  -- 5,621 random formulas (length 3-24, depth 1-4,
+  0-3 variables) plus K, T, 4: the five-world census standing in for the
+  paper's 5,624-formula corpus (Sec. 6), whose files are not available.
+* ``uneven_formulas``   -- 20,000 formulas, length and depth log-uniform in
+  [3, 64] and [1, 8], each with its own class and n_max (config "uneven").
+* ``separation_pairs``  -- 1,024 variable-free pairs: the 32 context pairs
+  (C^m b, C^(m+1) b) of the active-synthesis protocol (Sec. 7), (alpha_5,
+  alpha_6), and 991 seeded random pairs, half of them one-edit mutations.
+* ``proposal_formulas`` -- 10,000 formulas: 2,000 bases (length <= 21, depth
+  <= 10) and 8,000 Boolean compositions of them (Sec. 9 retrieval corpus).
+* ``sampled_valuations`` -- the S sampled valuations of layer n: output j of
+  the SplitMix64 stream (Steele, Lea, Flood 2014) for (seed, tag 1, n).
+
+Formula syntax: atoms ``p0``..``p3`` (``p``, ``q`` = p0, p1), ``T``, ``F``;
+unary ``~``, ``[]``, ``<>``; binary ``&``, ``|``, ``->`` (right
+associative).  Generated texts are fully parenthesised.
+"""
+import math
+import random
+
+import numpy as np
+
+K_AXIOM = "[](p -> q) -> ([]p -> []q)"
+T_AXIOM = "[]p -> p"
+FOUR_AXIOM = "[]p -> [][]p"
+AXIOMS = (K_AXIOM, T_AXIOM, FOUR_AXIOM)
+
+_M64 = (1 << 64) - 1
+_GAMMA = 0x9E3779B97F4A7C15
+
+
+def _mix(z):
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def splitmix_state(seed, tag, n):
+    """Start state of the SplitMix64 stream for (seed, tag, n)."""
+    return _mix((seed ^ (tag << 32) ^ n) & _M64)
+
+
+def splitmix_out(state, j):
+    """Output j (0-based) of SplitMix64 started at ``state``."""
+    return _mix((state + (j + 1) * _GAMMA) & _M64)
+
+
+def sampled_valuations(seed, n, S):
+    """uint32[S]: the sampled valuations of layer n (their low k*n bits are
+    used by a k-variable formula)."""
+    st = splitmix_state(seed, 1, n)
+    return np.array([splitmix_out(st, j) & 0xFFFFFFFF for j in range(S)], dtype=np.uint32)
+
+
+def valuation_table(seed, S, n_max=8):
+    """uint32[n_max+1][S]: row n = sampled_valuations(seed, n, S) (row 0 unused)."""
+    t = np.zeros((n_max + 1, max(S, 1)), dtype=np.uint32)
+    for n in range(1, n_max + 1):
+        if S:
+            t[n] = sampled_valuations(seed, n, S)
+    return t
+
+
+# ------------------------------------------------------------ formula trees
+
+def _feasible(L, d):
+    """Productions that can root a tree with exactly L nodes and modal depth
+    exactly d."""
+    out = []
+    if L == 1:
+        return ["leaf"] if d == 0 else []
+    if L - 1 >= d + 1 or (d == 0 and L - 1 >= 1):
+        out.append("~")
+    if d >= 1 and L - 1 >= d:
+        out += ["[]", "<>"]
+    if L >= 3 and L - 2 >= d + 1:
+        out += ["&", "|", "->"]
+    return out
+
+
+def _tree(rng, L, d):
+    prods = _feasible(L, d)
+    if not prods:
+        raise ValueError("no tree with %d nodes and depth %d" % (L, d))
+    p = rng.choice(prods)
+    if p == "leaf":
+        return ["leaf"]
+    if p == "~":
+        return ["~", _tree(rng, L - 1, d)]
+    if p in ("[]", "<>"):
+        return [p, _tree(rng, L - 1, d - 1)]
+    # binary: one side carries depth d, the other any feasible depth <= d
+    while True:
+        a = rng.randint(1, L - 2)
+        b = L - 1 - a
+        if rng.random() < 0.5:
+            if a >= d + 1:
+                da, db = d, rng.randint(0, min(d, b - 1))
+                break
+        else:
+            if b >= d + 1:
+                da, db = rng.randint(0, min(d, a - 1)), d
+                break
+    return [p, _tree(rng, a, da), _tree(rng, b, db)]
+
+
+def _leaves(t, acc):
+    if t[0] == "leaf":
+        acc.append(t)
+    else:
+        for c in t[1:]:
+            _leaves(c, acc)
+    return acc
+
+
+def _text(t):
+    op = t[0]
+    if op == "leaf":
+        return t[1]
+    if op in ("~", "[]", "<>"):
+        return op + _text(t[1])
+    return "(" + _text(t[1]) + " " + op + " " + _text(t[2]) + ")"
+
+
+def random_formula(rng, length, depth, k, const_p=0.2, atoms=None):
+    """A formula with exactly ``length`` nodes, modal depth exactly ``depth``
+    and highest variable p_(k-1) (variable-free when k == 0)."""
+    depth = min(depth, length - 1)
+    t = _tree(rng, length, depth)
+    leaves = _leaves(t, [])
+    if atoms is None:
+        atoms = ["p%d" % i for i in range(k)]
+    for lf in leaves:
+        if not atoms or rng.random() < const_p:
+            lf.append(rng.choice(["T", "F"]))
+        else:
+            lf.append(rng.choice(atoms))
+    if k > 0:
+        rng.choice(leaves)[1:] = [atoms[k - 1]]
+    return _text(t)
+
+
+def pr1_formulas(seed=1, count=64):
+    """64 formulas over p, q, T, F (length <= 12, depth <= 3) + K, T, 4."""
+    rng = random.Random(seed)
+    out = []
+    for _ in range(count):
+        L = rng.randint(3, 12)
+        d = rng.randint(0, 3)
+        k = rng.randint(0, 2)
+        out.append(random_formula(rng, L, d, k, const_p=0.25,
+                                  atoms=["p", "q"][:k] if k else None))
+    return out + list(AXIOMS)
+
+
+def census5_formulas(seed=2, count=5621):
+    """Five-world census corpus: length 3-24, depth 1-4, 0-3 variables."""
+    rng = random.Random(seed)
+    out = []
+    for _ in range(count):
+        L = rng.randint(3, 24)
+        d = rng.randint(1, 4)
+        k = rng.randint(0, 3)
+        out.append(random_formula(rng, L, d, k))
+    return out + list(AXIOMS)
+
+
+def _log_uniform_int(rng, lo, hi):
+    return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+
+
+def uneven_formulas(seed=3, count=20000):
+    """Uneven batch: (text, class, n_max) with length log-uniform 3-64, depth
+    log-uniform 1-8 (at most length-1), classes uniform over K/T/S4/S5 and
+    n_max uniform over {3, 4, 5}."""
+    rng = random.Random(seed)
+    out = []
+    for _ in range(count):
+        L = _log_uniform_int(rng, 3, 64)
+        d = min(_log_uniform_int(rng, 1, 8), L - 1)
+        k = rng.randint(0, 3)
+        cls = rng.choice(["K", "T", "S4", "S5"])
+        nmax = rng.choice([3, 4, 5])
+        out.append((random_formula(rng, L, d, k), cls, nmax))
+    return out
+
+
+def alpha(m):
+    """alpha_m = ([]<>)^m T."""
+    return "[]<>" * m + "T"
+
+
+def context_pairs():
+    """The 32 active-synthesis pairs (C^m b, C^(m+1) b) of Sec. 7."""
+    out = []
+    for C in ("[]<>", "<>[]", "[][]", "<><>"):
+        for b in ("T", "F"):
+            for m in range(1, 5):
+                out.append((C * m + b, C * (m + 1) + b))
+    return out
+
+
+def _mutate(rng, text):
+    """One edit of a modal word over a constant: flip, insert or delete one
+    operator, or flip the base constant."""
+    body, base = text[:-1], text[-1]
+    ops = [body[i:i + 2] for i in range(0, len(body), 2)]
+    r = rng.random()
+    if r < 0.1:
+        base = "F" if base == "T" else "T"
+    elif r < 0.5 and ops:
+        i = rng.randrange(len(ops))
+        ops[i] = "<>" if ops[i] == "[]" else "[]"
+    elif r < 0.75 or not ops:
+        ops.insert(rng.randrange(len(ops) + 1), rng.choice(["[]", "<>"]))
+    else:
+        del ops[rng.randrange(len(ops))]
+    return "".join(ops) + base
+
+
+def separation_pairs(seed=4, count=1024):
+    """1,024 variable-free pairs: 32 context pairs, (alpha_5, alpha_6), then
+    seeded random pairs (half independent, half one-edit mutations)."""
+    rng = random.Random(seed)
+    out = context_pairs() + [(alpha(5), alpha(6))]
+    ctx = context_pairs()
+    while len(out) < count:
+        if len(out) % 2 == 0:
+            a, b = rng.choice(ctx)
+            src = rng.choice([a, b])
+            out.append((src, _mutate(rng, src)))
+        else:
+            L1, L2 = rng.randint(3, 14), rng.randint(3, 14)
+            d1, d2 = rng.randint(1, min(6, L1 - 1)), rng.randint(1, min(6, L2 - 1))
+            out.append((random_formula(rng, L1, d1, 0), random_formula(rng, L2, d2, 0)))
+    return out[:count]
+
+
+def proposal_formulas(seed=5, count=10000, bases=2000):
+    """Retrieval corpus: ``bases`` base formulas (length <= 21, depth <= 10,
+    0-2 variables) and Boolean compositions (&, |, -> of two bases, or ~)."""
+    rng = random.Random(seed)
+    base = []
+    for i in range(bases):
+        L = rng.randint(2, 21)
+        d = rng.randint(0, min(10, L - 1))
+        k = rng.randint(0, 2)
+        base.append(random_formula(rng, L, d, k))
+    out = list(base)
+    while len(out) < count:
+        r = rng.random()
+        a = rng.choice(base)
+        if r < 0.1:
+            out.append("~(" + a + ")")
+        else:
+            b = rng.choice(base)
+            op = rng.choice(["&", "|", "->"])
+            out.append("(" + a + ") " + op + " (" + b + ")")
+    return out
+
+
+def nodes(text):
+    """Node count |phi| of a generated text (atoms, constants, operators)."""
+    import re
+    return len(re.findall(r"p\d+|[pqrs](?!\d)|T|F|~|\[\]|<>|&|\||->", text))
