@@ -1,0 +1,260 @@
+/*
+ * mk.h -- C ABI of libmk: exhaustive evaluation of modal formulas over every
+ * labelled Kripke frame up to n worlds, on one GB300 GPU (sm_103a).
+ *
+ * Conventions for every call
+ *   - Return value: 0 (MK_OK) on success, a negative MK_E_* code otherwise;
+ *     mk_strerror() gives its text.  A call that fails leaves its outputs
+ *     undefined and launches nothing after the failing step.
+ *   - Pointers named d_* are device pointers (any allocator; the Python
+ *     binding uses PyTorch).  Pointers named h_* (and all other pointers) are
+ *     host pointers.  The caller owns every buffer; the library allocates no
+ *     device memory: scratch comes from a caller-provided workspace of the size
+ *     the matching *_workspace_size() call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device calls are asynchronous on it; outputs are valid once
+ *     the stream has been synchronised.
+ *   - Device-side failures (a malformed program, a limit exceeded inside a
+ *     kernel, an iteration limit reached) are OR-ed as MK_ST_* bits into the
+ *     caller's int32 device word d_status (clear it before the call);
+ *     mk_status_error() maps a read-back status to an MK_E_* code.
+ *   - Calls on distinct buffers and streams are thread-safe: the library has
+ *     no global state.
+ *
+ * Encodings (the readings of the paper behind them are listed in the design doc)
+ *   - World w of an n-world frame is bit w of a mask; full = 2^n - 1 (Sec. 3).
+ *   - Frame (K) index f: R(w,v) holds iff bit w*n+v of f is set, so the
+ *     successor mask succ[w] is bits [w*n, w*n+n) of f.
+ *   - Valuation index x: p_i holds at w iff bit i*n+w of x is set.
+ *   - k = 1 + the highest variable index in the formula (0 if none).
+ *   - A layer's valuations are exhaustive (x = 0 .. 2^(k n)-1) when S == 0,
+ *     k <= 1 or 2^(k n) <= S; otherwise the S sampled values of that layer
+ *     (their low k*n bits), in slot order, counted with multiplicity.
+ */
+#ifndef MK_H
+#define MK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- limits */
+#define MK_MAX_NODES 64          /* |phi| of a compiled formula               */
+#define MK_MAX_CODE 96           /* instructions per program (<= nodes + pushes) */
+#define MK_MAX_STACK 4           /* saved truth sets per program               */
+#define MK_MAX_VARS 4            /* p0..p3 (paper's limit, Sec. 12)            */
+#define MK_MAX_WORLDS_EXH 6      /* exhaustive frames: K index < 2^36          */
+#define MK_MAX_WORLDS_SAMPLED 8  /* sampled separation frames                  */
+#define MK_MAX_CERT_WORLDS 32    /* certificates (u32 successor masks)         */
+
+/* ----------------------------------------------------------- error codes */
+#define MK_OK 0
+#define MK_E_SYNTAX (-1)     /* formula text does not parse                   */
+#define MK_E_TOO_LONG (-2)   /* more than MK_MAX_NODES nodes / MK_MAX_CODE ops */
+#define MK_E_VARS (-3)       /* variable index >= MK_MAX_VARS                 */
+#define MK_E_SLOTS (-4)      /* needs more than MK_MAX_STACK stack entries     */
+#define MK_E_ARG (-5)        /* invalid argument or configuration             */
+#define MK_E_WORKSPACE (-6)  /* workspace missing or too small                */
+#define MK_E_CUDA (-7)       /* a CUDA runtime call failed                    */
+#define MK_E_PROGRAM (-8)    /* device saw a malformed program                */
+#define MK_E_LIMIT (-9)      /* a size limit was exceeded (e.g. k*n)          */
+#define MK_E_INTERNAL (-10)  /* internal consistency check failed             */
+#define MK_E_TIMEOUT (-11)   /* a bounded device wait ran out                 */
+
+/* device status bits (OR-ed into *d_status) */
+#define MK_ST_PROGRAM 1u     /* malformed program: its results are not valid  */
+#define MK_ST_LIMIT 2u       /* exhaustive valuations with k*n > 24           */
+#define MK_ST_INTERNAL 4u    /* class-table size mismatch or similar          */
+#define MK_ST_TIMEOUT 8u     /* a bounded wait gave up                        */
+
+/* ----------------------------------------------------- frame classes */
+#define MK_CLASS_K 1u        /* all frames                                    */
+#define MK_CLASS_T 2u        /* reflexive                                     */
+#define MK_CLASS_S4 4u       /* reflexive and transitive (preorders)          */
+#define MK_CLASS_S5 8u       /* equivalence relations                         */
+
+/* --------------------------------------------------- compiled programs */
+/* A program is postfix code for an accumulator machine over truth sets (the
+   recurrence of Thm. 1): A is the current truth set (one n-world set per
+   register word lane), st[0..MK_MAX_STACK) a small stack of saved sets.
+   Instruction byte = op | operand << 4; the operand is a variable index i
+   or a stack depth d:
+     LDV i   A = [[p_i]]            LDT  A = W              LDF  A = {}
+     NOT     A = W \ A              BOX  A = {w : succ[w] subset of A}
+     DIA     A = {w : succ[w] meets A}          (Lemma 1, eqs. box/dia)
+     PUSH d  st[d] = A
+     AND_S d / OR_S d / IFF_S d   A = st[d] op A
+     IMP_S d  A = st[d] -> A      RIMP_S d  A = A -> st[d]
+     AND_V i / OR_V i             A = A op [[p_i]]
+     IMP_V i  A = A -> [[p_i]]    RIMP_V i  A = [[p_i]] -> A
+   A program ends with the formula's truth set in A. */
+enum {
+    MK_OP_LDV = 0, MK_OP_LDT = 1, MK_OP_LDF = 2, MK_OP_NOT = 3, MK_OP_BOX = 4, MK_OP_DIA = 5,
+    MK_OP_PUSH = 6, MK_OP_AND_S = 7, MK_OP_OR_S = 8, MK_OP_IMP_S = 9, MK_OP_RIMP_S = 10,
+    MK_OP_IFF_S = 11, MK_OP_AND_V = 12, MK_OP_OR_V = 13, MK_OP_IMP_V = 14, MK_OP_RIMP_V = 15,
+    MK_NUM_OPS = 16
+};
+
+typedef struct {
+    uint16_t nodes;        /* |phi|: node count of the source text          */
+    uint8_t n_instr;       /* instructions in code[]                        */
+    uint8_t nvars;         /* k                                             */
+    uint8_t modal_depth;   /* nesting depth of []/<> in the source          */
+    uint8_t depth;         /* stack entries used (<= MK_MAX_STACK)          */
+    uint8_t n_modal;       /* BOX/DIA instructions                          */
+    uint8_t n_bool;        /* NOT and binary instructions                   */
+    uint8_t code[MK_MAX_CODE];
+} mk_program;              /* 104 bytes, plain data                         */
+
+/* Compile formula text to a program (host).  Grammar: atoms p0..p3 (p, q, r,
+   s = p0..p3), T, F; unary ~ ! not [] box <> dia; binary & and, | or, ->
+   (right associative), tightest first; parentheses.  Constant subformulas are
+   folded (e.g. []T = T, <>F = F), which leaves every truth set unchanged.
+   *err_pos (may be NULL) receives the byte offset of a syntax error.
+   Formula grammar and node count: Sec. 2; postfix programs: Sec. 4. */
+int mk_compile(const char *text, mk_program *out, int32_t *err_pos);
+
+/* Compile "phi <-> psi" into one program whose truth set is the set of
+   worlds where phi and psi agree (the biconditional of Prop. 6). */
+int mk_compile_iff(const char *phi, const char *psi, mk_program *out, int32_t *err_pos);
+
+/* ----------------------------------------------------------- the census */
+typedef struct {
+    uint16_t block;        /* threads per CTA: 128, 256 or 512 (0 = 256)    */
+    uint16_t tile;         /* formulas per CTA, 1..64 (0 = 16)              */
+    uint16_t words;        /* 32-frame words per thread, 1..8 (0 = 1)       */
+    uint16_t persistent;   /* 1 = one persistent launch over a work queue   */
+} mk_tune;
+
+typedef struct {
+    uint32_t classes;          /* MK_CLASS_* bits                                */
+    uint8_t n_min, n_max;      /* 1 <= n_min <= n_max <= 6                       */
+    uint8_t max_depth;         /* largest program depth in the batch (0 = the    */
+                               /* limit MK_MAX_STACK); sizes the device stack;   */
+                               /* a deeper program sets MK_ST_PROGRAM            */
+    uint8_t reserved;
+    uint32_t samples;          /* S (0 = always exhaustive)                      */
+    uint32_t reserved2;
+    const uint32_t *d_samples; /* device [(n_max+1) * S]: row n = layer n's S    */
+                               /* sampled valuations; NULL iff S == 0            */
+    uint64_t frame_lo;         /* only frames with K index in [frame_lo,         */
+    uint64_t frame_hi;         /*  frame_hi); 0, UINT64_MAX = all                */
+    mk_tune tune;              /* zeros = defaults                               */
+} mk_census_cfg;
+
+typedef struct {
+    uint64_t cm_count;         /* refuted (frame, valuation) pairs               */
+    uint64_t frames_refuted;   /* frames with at least one refuted valuation     */
+    uint64_t witness_key;      /* least (frame, valuation, world), packed as     */
+                               /* f << 27 | x << 3 | w (x: valuation index or    */
+                               /* sample slot); UINT64_MAX = no countermodel     */
+} mk_result;
+
+/* Workspace bytes mk_census needs for this configuration and batch. */
+size_t mk_census_workspace_size(const mk_census_cfg *cfg, int32_t nprog);
+
+/* Census (Alg. 1 over every selected (class, n) layer, Thm. 4): for each
+   program p, each selected class c (in the order K, T, S4, S5) and each
+   n in [n_min, n_max], writes
+       d_out[(p * ncls + c) * (n_max - n_min + 1) + (n - n_min)]
+   where ncls = number of selected classes.  d_progs: device [nprog]
+   programs from mk_compile.  The refuted flag is cm_count > 0; the minimal
+   countermodel size is the least n with cm_count > 0. */
+int mk_census(const mk_program *d_progs, int32_t nprog, const mk_census_cfg *cfg,
+              mk_result *d_out, int32_t *d_status, void *d_workspace, size_t ws_bytes,
+              void *stream);
+
+/* Number of class-c frames on n worlds that mk_census enumerates (K: 2^(n^2),
+   T: 2^(n^2-n), S4: preorders, S5: equivalence relations); 0 if n > 6. */
+uint64_t mk_class_frames(uint32_t cls, int32_t n);
+
+/* ------------------------------------------------------- certificates */
+typedef struct {
+    const char *phi;           /* formula text                                   */
+    const char *psi;           /* NULL: countermodel certificate for phi;        */
+                               /* else: a world where phi and psi disagree       */
+    uint8_t n;                 /* worlds, 1..32                                  */
+    uint8_t cls;               /* 0 K, 1 T, 2 S4, 3 S5: the frame must be in it  */
+    uint8_t world;             /* the pointed world                              */
+    uint8_t reserved;
+    uint32_t succ[MK_MAX_CERT_WORLDS];  /* successor masks                       */
+    uint32_t val[MK_MAX_VARS];          /* variable masks                        */
+} mk_cert;
+
+/* Certificate check (Def. 1, Prop. 3), host only: its own parser and a
+   recursive evaluator over explicit successor sets, sharing no code with the
+   compiler or the kernels.  Returns 1 if valid (frame in class, and phi false
+   at world -- or phi and psi differ there), 0 if not, < 0 if malformed. */
+int mk_certify(const mk_cert *c);
+
+/* Decode a census witness key of program h_prog (host copy) on the class-cls,
+   n-world layer into a certificate (phi text supplied by the caller).
+   h_samples_n: the layer's S sampled valuations (host), NULL iff S == 0. */
+int mk_witness_cert(const mk_program *h_prog, const char *phi, uint32_t cls, int32_t n,
+                    uint32_t samples, const uint32_t *h_samples_n, uint64_t key,
+                    mk_cert *out);
+
+/* ------------------------------------------------------- separation */
+typedef struct {
+    uint8_t n_exh_min, n_exh_max;  /* exhaustive K sizes scanned, 1..6          */
+    uint8_t n_smp_min, n_smp_max;  /* sampled sizes, 7..8 (0, 0 = none)         */
+    uint32_t samples;              /* valuation samples S (as in the census)    */
+    const uint32_t *d_samples;     /* device [(8+1) * S] or NULL iff S == 0     */
+    uint64_t frames_per_n;         /* sampled relations per sampled size        */
+    uint64_t seed;                 /* seed of the relation stream               */
+    uint64_t frame_lo, frame_hi;   /* K-index range of exhaustive sizes         */
+    mk_tune tune;
+} mk_separate_cfg;
+
+/* Distinguishing-pair search (Def. 2, Prop. 6): for each pair i, the least
+   (n, frame, valuation, world) at which phi_i and psi_i take different
+   truth values, over the K frames of n_exh_min..n_exh_max worlds in K-index
+   order, then the sampled relations of n_smp_min..n_smp_max worlds in sample
+   order (sizes are searched in that order; a pair with a split at one size is
+   not searched at later sizes).  Writes d_split[i] = the packed key
+       n << 60 | f << 24 | x << 3 | w
+   (f: K index or sample number < 2^36; x < 2^21; w < 8), UINT64_MAX if the
+   pair agrees everywhere searched.  Relations of sampled sizes come from
+   mk_sample_relation(seed, n, s). */
+size_t mk_separate_workspace_size(const mk_separate_cfg *cfg, int32_t npairs);
+int mk_separate(const mk_program *d_phi, const mk_program *d_psi, int32_t npairs,
+                const mk_separate_cfg *cfg, uint64_t *d_split, int32_t *d_status,
+                void *d_workspace, size_t ws_bytes, void *stream);
+
+/* The row-major edge mask of sampled relation s on n <= 8 worlds: nine
+   SplitMix64 draws per sample (Steele, Lea, Flood 2014), draw 0 sets the
+   edge threshold t in [26, 128] (p = t/256 in [0.1, 0.5]), edge e is present
+   iff byte e%8 of draw 1+e/8 is below t (Sec. 7, Erdos-Renyi frames). */
+uint64_t mk_sample_relation(uint64_t seed, int32_t n, uint64_t s);
+
+/* Decode a split key into a certificate for (phi, psi) (host). */
+int mk_split_cert(const mk_program *h_phi, const mk_program *h_psi, const char *phi,
+                  const char *psi, uint64_t seed, uint32_t samples,
+                  const uint32_t *h_samples_n, uint64_t key, mk_cert *out);
+
+/* Kernel launches one mk_census call with this configuration issues
+   (result initialisation, class-list construction, one per layer). */
+int32_t mk_census_launches(const mk_census_cfg *cfg, int32_t nprog);
+
+/* ------------------------------------------------------ calibration */
+/* Logic-op issue ceiling (the roofline denominator of the census; Sec. 10
+   measures the same uint32 logic ceiling): launches blocks x threads
+   threads, each running independent chains of three-input logic ops for
+   `iters` iterations; d_sink is a device word array of `blocks` entries. */
+int mk_calibrate_lop3(uint32_t *d_sink, int32_t blocks, int32_t threads, uint32_t iters,
+                      uint32_t seed, void *stream);
+/* Logic ops one such launch performs. */
+uint64_t mk_calibrate_ops_per_launch(int32_t blocks, int32_t threads, uint32_t iters);
+
+/* ------------------------------------------------------------- misc */
+const char *mk_strerror(int code);
+int mk_status_error(int32_t status);   /* MK_OK or the MK_E_* for status bits */
+int mk_version(void);                  /* ABI version                         */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MK_H */

@@ -1,0 +1,394 @@
+// mk_separate.cu -- distinguishing-pair search (Def. 2, Prop. 6).
+//
+// A pair (phi, psi) is separated on a pointed model iff their truth sets
+// differ there, i.e. iff the biconditional phi <-> psi is refuted (Prop. 6).
+// The kernel runs both programs on the same bit-sliced frame words (U words
+// per thread, one valuation at a time), takes d[w] = t_phi[w] ^ t_psi[w]
+// per world and keeps the least (frame, valuation, world) with a set bit,
+// as one packed u64 key per pair that also carries n in its top bits; a
+// global atomicMin merges CTAs.
+//
+// Sizes are launched in increasing n; the K frames of the largest sizes are
+// launched in ascending chunks.  A CTA reads each pair's current key when it
+// stages the pair and drops pairs whose key is already below the least key
+// the CTA could produce (a split at a smaller n, or at an earlier chunk), so
+// work on a pair stops soon after its first split ("done" flags read without
+// any wait).  Sampled sizes (7, 8) generate their relations on the device
+// from the counter-based SplitMix64 stream, 32 samples per frame word.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "mk.h"
+#include "mk_eval.cuh"
+
+namespace mkd {
+
+constexpr int SEP_ROW_CAP = 128;
+
+struct SepArgs {
+    const mk_program *phi;
+    const mk_program *psi;
+    int32_t npairs;
+    int32_t tile;
+    const uint32_t *samples;   // this size's sampled valuations (device)
+    uint32_t S;
+    int32_t sampled;           // 1: frames are sampled relations
+    uint64_t rel_state;        // SplitMix64 state of the relation stream
+    uint64_t word_lo, word_hi; // frame words of this launch
+    uint64_t nframes;          // frames (K) or samples of this size
+    uint64_t f_lo, f_hi;       // K-index filter (exhaustive sizes)
+    int32_t full_range;
+    uint64_t *split;
+    int32_t *status;
+};
+
+template <int N, int U, int BLOCK>
+struct SepSmem {
+    static constexpr size_t code_bytes(int tile) { return ((size_t)tile * MK_MAX_CODE * 2 + 16 + 15) & ~(size_t)15; }
+    static constexpr size_t meta_bytes(int tile) { return (size_t)tile * 24; }   // 4 int + u64
+    static constexpr size_t row_bytes() { return (size_t)SEP_ROW_CAP * RowShape<N>::WORDS * 4; }
+    static constexpr size_t stack_bytes() { return (size_t)MK_MAX_STACK * U * N * BLOCK * 4; }
+    static size_t total(int tile) { return code_bytes(tile) + meta_bytes(tile) + row_bytes() + stack_bytes(); }
+};
+
+// Edge words of 32 sampled relations s = base .. base+31 (lane l <- s).
+template <int N>
+__device__ __forceinline__ uint32_t sampled_frame_word(uint64_t state, uint64_t base, uint64_t nframes,
+                                                       uint32_t (&E)[N * N]) {
+#pragma unroll
+    for (int e = 0; e < N * N; ++e) E[e] = 0;
+    uint32_t valid = 0;
+    for (int l = 0; l < 32; ++l) {
+        const uint64_t s = base + (uint64_t)l;
+        if (s >= nframes) break;
+        valid |= 1u << l;
+        const uint64_t d0 = sm_out(state, 9 * s);
+        const uint64_t t = 26 + (((d0 >> 32) * 103ull) >> 32);
+#pragma unroll
+        for (int g = 0; g < (N * N + 7) / 8; ++g) {
+            const uint64_t d = sm_out(state, 9 * s + 1 + (uint64_t)g);
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                if (g * 8 + b < N * N) E[g * 8 + b] |= (uint32_t)(((d >> (8 * b)) & 0xFFu) < t) << l;
+            }
+        }
+    }
+    return valid;
+}
+
+template <int N, int U, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
+    using SM = SepSmem<N, U, BLOCK>;
+    constexpr int RW = RowShape<N>::WORDS;
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ int s_active;
+    const int tile = a.tile;
+    uint8_t *s_phi = smem;
+    uint8_t *s_psi = smem + (size_t)tile * MK_MAX_CODE;
+    int *s_na = (int *)(smem + SM::code_bytes(tile));
+    int *s_nb = s_na + tile;
+    int *s_k = s_nb + tile;
+    int *s_pad = s_k + tile;
+    unsigned long long *s_key = (unsigned long long *)(s_pad + tile);
+    uint32_t *s_rows = (uint32_t *)(smem + SM::code_bytes(tile) + SM::meta_bytes(tile));
+    uint32_t *s_stack = (uint32_t *)((uint8_t *)s_rows + SM::row_bytes()) + threadIdx.x;
+
+    const uint64_t cta_word0 = a.word_lo + (uint64_t)blockIdx.x * BLOCK * U;
+    const unsigned long long floor_key =
+        ((unsigned long long)N << 60) | ((unsigned long long)(cta_word0 << 5) << 24);
+    if (threadIdx.x == 0) s_active = 0;
+    __syncthreads();
+    const int p0 = blockIdx.y * tile;
+    const int np = min(tile, a.npairs - p0);
+    for (int i = threadIdx.x; i < np; i += BLOCK) {
+        const mk_program &pa = a.phi[p0 + i], &pb = a.psi[p0 + i];
+        int ok = program_ok(pa) && program_ok(pb);
+        if (!ok && blockIdx.x == 0) atomicOr(a.status, (int)MK_ST_PROGRAM);
+        const int k = pa.nvars > pb.nvars ? pa.nvars : pb.nvars;
+        const bool exh = exhaustive_vals(k, N, a.S);
+        const uint64_t nval = exh ? (1ull << (k * N)) : a.S;
+        if (ok && (nval > (1ull << 21) || (exh && k * N > 21))) {
+            ok = 0;
+            if (blockIdx.x == 0) atomicOr(a.status, (int)MK_ST_LIMIT);
+        }
+        // a split already below this CTA's least key ends the pair here
+        if (ok && ((volatile unsigned long long *)a.split)[p0 + i] < floor_key) ok = 0;
+        s_na[i] = ok ? pa.n_instr : -1;
+        s_nb[i] = pb.n_instr;
+        s_k[i] = k;
+        s_key[i] = ~0ull;
+        if (ok) atomicAdd(&s_active, 1);
+    }
+    __syncthreads();
+    if (s_active == 0) return;
+    for (int i = threadIdx.x; i < np * MK_MAX_CODE / 4; i += BLOCK) {
+        const int pi = i / (MK_MAX_CODE / 4), wi = i % (MK_MAX_CODE / 4);
+        ((uint32_t *)s_phi)[i] = ((const uint32_t *)a.phi[p0 + pi].code)[wi];
+        ((uint32_t *)s_psi)[i] = ((const uint32_t *)a.psi[p0 + pi].code)[wi];
+    }
+    if (threadIdx.x < 4) ((uint32_t *)(s_psi + (size_t)np * MK_MAX_CODE))[threadIdx.x] = 0;
+    // the bytes after phi's last program are psi's first: readable
+
+    uint32_t E[U][N * N];
+    uint32_t valid[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const uint64_t word = cta_word0 + (uint64_t)threadIdx.x * U + u;
+        const uint64_t base = word << 5;
+        valid[u] = 0;
+        if (word < a.word_hi) {
+            if (a.sampled) {
+                valid[u] = sampled_frame_word<N>(a.rel_state, base, a.nframes, E[u]);
+            } else {
+                if constexpr (N <= MK_MAX_WORLDS_EXH) k_frame_word<N>(word, E[u]);
+                if (base < a.nframes) {
+                    const uint64_t left = a.nframes - base;
+                    valid[u] = left >= 32 ? 0xFFFFFFFFu : ((1u << left) - 1u);
+                }
+                if (!a.full_range) {
+                    for (int l = 0; l < 32; ++l)
+                        if (base + l < a.f_lo || base + l >= a.f_hi) valid[u] &= ~(1u << l);
+                }
+            }
+        }
+        if (!valid[u]) {
+#pragma unroll
+            for (int e = 0; e < N * N; ++e) E[u][e] = 0;
+        }
+    }
+    const int lane = threadIdx.x & 31;
+    int rows_kind = -1;
+    uint32_t rows_c0 = 0;
+    __syncthreads();
+
+    for (int fi = 0; fi < np; ++fi) {
+        const int na = s_na[fi];
+        if (na < 0) continue;
+        const int nb = s_nb[fi];
+        const int k = s_k[fi];
+        const bool exh = exhaustive_vals(k, N, a.S);
+        const uint32_t nval = exh ? (1u << (k * N)) : a.S;
+        const uint8_t *ca = s_phi + fi * MK_MAX_CODE, *cb = s_psi + fi * MK_MAX_CODE;
+        int best_o = U * 32, best_w = 0;     // o = u * 32 + lane: ascending frames
+        uint32_t best_j = 0;
+        for (uint32_t c0 = 0; c0 < nval; c0 += SEP_ROW_CAP) {
+            const uint32_t cn = min((uint32_t)SEP_ROW_CAP, nval - c0);
+            if (rows_kind != (exh ? 0 : 1) || rows_c0 != c0) {
+                __syncthreads();
+                constexpr int W = RowShape<N>::WORDS;
+                const uint32_t rows = exh ? (uint32_t)SEP_ROW_CAP : min((uint32_t)SEP_ROW_CAP, a.S - c0);
+                for (uint32_t i = threadIdx.x; i < rows * W; i += BLOCK) {
+                    const uint32_t j = c0 + i / W;
+                    s_rows[i] = atom_row_word<N>(exh ? j : a.samples[j], (int)(i % W));
+                }
+                __syncthreads();
+                rows_kind = exh ? 0 : 1;
+                rows_c0 = c0;
+            }
+            for (uint32_t jj = 0; jj < cn && best_o > 0; ++jj) {
+                const uint32_t *rows[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) rows[u] = s_rows + jj * RW;
+                uint32_t A[U][N], B[U][N];
+                run_program<N, U, U, BLOCK>(ca, na, rows, E, s_stack, A);
+                run_program<N, U, U, BLOCK>(cb, nb, rows, E, s_stack, B);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    uint32_t any = 0;
+#pragma unroll
+                    for (int w = 0; w < N; ++w) any |= A[u][w] ^ B[u][w];
+                    any &= valid[u];
+                    if (any) {
+                        const int o = u * 32 + __ffs(any) - 1;
+                        if (o < best_o) {
+                            const int l = o - u * 32;
+                            best_o = o;
+                            best_j = c0 + jj;
+                            int bw = 0;
+#pragma unroll
+                            for (int w = N - 1; w >= 0; --w)
+                                if (((A[u][w] ^ B[u][w]) >> l) & 1u) bw = w;
+                            best_w = bw;
+                        }
+                    }
+                }
+            }
+        }
+        const uint32_t hit = __ballot_sync(0xFFFFFFFFu, best_o < U * 32);
+        if (hit) {
+            // threads hold ascending frame words, so the lowest hit lane wins
+            const int src_lane = __ffs(hit) - 1;
+            uint64_t my = 0;
+            if (lane == src_lane) {
+                const uint64_t f = ((cta_word0 + (uint64_t)threadIdx.x * U) << 5) + (uint64_t)best_o;
+                my = ((uint64_t)N << 60) | (f << 24) | ((uint64_t)best_j << 3) | (uint64_t)best_w;
+            }
+            const uint64_t key = __shfl_sync(0xFFFFFFFFu, my, src_lane);
+            if (lane == 0) atomicMin(&s_key[fi], (unsigned long long)key);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < np; i += BLOCK)
+        if (s_key[i] != ~0ull) atomicMin((unsigned long long *)&a.split[p0 + i], s_key[i]);
+}
+
+__global__ void init_split_kernel(uint64_t *split, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) split[i] = ~0ull;
+}
+
+}  // namespace mkd
+
+namespace {
+
+using namespace mkd;
+
+constexpr int SEP_BLOCK = 256;
+
+template <int N>
+constexpr int sep_units() { return N <= 6 ? 2 : 1; }
+
+template <int N>
+void launch_sep(const SepArgs &a, cudaStream_t s) {
+    constexpr int U = sep_units<N>();
+    const uint64_t words = a.word_hi > a.word_lo ? a.word_hi - a.word_lo : 0;
+    if (words == 0 || a.npairs == 0) return;
+    const uint64_t per_cta = (uint64_t)SEP_BLOCK * U;
+    dim3 grid((unsigned)((words + per_cta - 1) / per_cta), (unsigned)((a.npairs + a.tile - 1) / a.tile));
+    const size_t sm = SepSmem<N, U, SEP_BLOCK>::total(a.tile);
+    auto kern = separate_kernel<N, U, SEP_BLOCK>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    kern<<<grid, SEP_BLOCK, sm, s>>>(a);
+}
+
+void launch_sep_n(int n, const SepArgs &a, cudaStream_t s) {
+    switch (n) {
+    case 1: launch_sep<1>(a, s); break;
+    case 2: launch_sep<2>(a, s); break;
+    case 3: launch_sep<3>(a, s); break;
+    case 4: launch_sep<4>(a, s); break;
+    case 5: launch_sep<5>(a, s); break;
+    case 6: launch_sep<6>(a, s); break;
+    case 7: launch_sep<7>(a, s); break;
+    case 8: launch_sep<8>(a, s); break;
+    }
+}
+
+int check_sep(const mk_separate_cfg *cfg, int32_t npairs) {
+    if (!cfg || npairs < 0) return MK_E_ARG;
+    if (cfg->n_exh_max > MK_MAX_WORLDS_EXH || cfg->n_exh_min > cfg->n_exh_max) return MK_E_ARG;
+    if (cfg->n_exh_max && cfg->n_exh_min < 1) return MK_E_ARG;
+    if (cfg->n_smp_max) {
+        if (cfg->n_smp_min < 1 || cfg->n_smp_min > cfg->n_smp_max || cfg->n_smp_max > MK_MAX_WORLDS_SAMPLED)
+            return MK_E_ARG;
+        if (cfg->n_exh_max && cfg->n_smp_min <= cfg->n_exh_max) return MK_E_ARG;
+        if (cfg->frames_per_n >= (1ull << 36)) return MK_E_ARG;
+    }
+    if ((cfg->samples == 0) != (cfg->d_samples == nullptr)) return MK_E_ARG;
+    if (cfg->frame_lo > cfg->frame_hi) return MK_E_ARG;
+    const mk_tune &t = cfg->tune;
+    if (t.block && t.block != SEP_BLOCK) return MK_E_ARG;
+    if (t.tile > 64) return MK_E_ARG;
+    return MK_OK;
+}
+
+}  // namespace
+
+extern "C" size_t mk_separate_workspace_size(const mk_separate_cfg *cfg, int32_t npairs) {
+    (void)cfg;
+    (void)npairs;
+    return 0;
+}
+
+extern "C" uint64_t mk_sample_relation(uint64_t seed, int32_t n, uint64_t s) {
+    if (n < 1 || n > MK_MAX_WORLDS_SAMPLED) return 0;
+    return sample_relation(sm_stream(seed, 2, (uint64_t)n), n, s);
+}
+
+extern "C" int mk_separate(const mk_program *d_phi, const mk_program *d_psi, int32_t npairs,
+                           const mk_separate_cfg *cfg, uint64_t *d_split, int32_t *d_status,
+                           void *d_workspace, size_t ws_bytes, void *stream) {
+    (void)d_workspace;
+    (void)ws_bytes;
+    int rc = check_sep(cfg, npairs);
+    if (rc != MK_OK) return rc;
+    if (npairs > 0 && (!d_phi || !d_psi || !d_split)) return MK_E_ARG;
+    if (!d_status) return MK_E_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (npairs == 0) return MK_OK;
+    init_split_kernel<<<(npairs + 255) / 256, 256, 0, s>>>(d_split, npairs);
+    const int tile = cfg->tune.tile ? cfg->tune.tile : 16;
+    const uint64_t chunk_words = 1ull << 22;
+
+    SepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.phi = d_phi;
+    a.psi = d_psi;
+    a.npairs = npairs;
+    a.tile = tile;
+    a.S = cfg->samples;
+    a.split = d_split;
+    a.status = d_status;
+    if (cfg->n_exh_max) {
+        for (int n = cfg->n_exh_min; n <= cfg->n_exh_max; ++n) {
+            const uint64_t kf = 1ull << (n * n);
+            const uint64_t hi = cfg->frame_hi < kf ? cfg->frame_hi : kf;
+            a.samples = cfg->samples ? cfg->d_samples + (size_t)n * cfg->samples : nullptr;
+            a.sampled = 0;
+            a.nframes = kf;
+            a.f_lo = cfg->frame_lo;
+            a.f_hi = cfg->frame_hi;
+            a.full_range = (cfg->frame_lo == 0 && cfg->frame_hi >= kf) ? 1 : 0;
+            const uint64_t w0 = cfg->frame_lo / 32, w1 = cfg->frame_lo >= hi ? w0 : (hi + 31) / 32;
+            for (uint64_t w = w0; w < w1; w += chunk_words) {
+                a.word_lo = w;
+                a.word_hi = w + chunk_words < w1 ? w + chunk_words : w1;
+                launch_sep_n(n, a, s);
+            }
+        }
+    }
+    if (cfg->n_smp_max) {
+        for (int n = cfg->n_smp_min; n <= cfg->n_smp_max; ++n) {
+            a.samples = cfg->samples ? cfg->d_samples + (size_t)n * cfg->samples : nullptr;
+            a.sampled = 1;
+            a.rel_state = sm_stream(cfg->seed, 2, (uint64_t)n);
+            a.nframes = cfg->frames_per_n;
+            a.full_range = 1;
+            const uint64_t w1 = (cfg->frames_per_n + 31) / 32;
+            const uint64_t cw = 1ull << 18;
+            for (uint64_t w = 0; w < w1; w += cw) {
+                a.word_lo = w;
+                a.word_hi = w + cw < w1 ? w + cw : w1;
+                launch_sep_n(n, a, s);
+            }
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? MK_OK : MK_E_CUDA;
+}
+
+extern "C" int mk_split_cert(const mk_program *h_phi, const mk_program *h_psi, const char *phi,
+                             const char *psi, uint64_t seed, uint32_t samples, const uint32_t *h_samples_n,
+                             uint64_t key, mk_cert *out) {
+    if (!h_phi || !h_psi || !phi || !psi || !out || key == ~0ull) return MK_E_ARG;
+    const int n = (int)(key >> 60);
+    const uint64_t f = (key >> 24) & ((1ull << 36) - 1);
+    const uint32_t j = (uint32_t)((key >> 3) & ((1u << 21) - 1));
+    const int w = (int)(key & 7u);
+    if (n < 1 || n > MK_MAX_WORLDS_SAMPLED || w >= n) return MK_E_ARG;
+    const int k = h_phi->nvars > h_psi->nvars ? h_phi->nvars : h_psi->nvars;
+    const bool exh = exhaustive_vals(k, n, samples);
+    if (!exh && !h_samples_n) return MK_E_ARG;
+    const uint64_t rel = n <= MK_MAX_WORLDS_EXH ? f : sample_relation(sm_stream(seed, 2, (uint64_t)n), n, f);
+    const uint32_t x = exh ? j : h_samples_n[j];
+    const uint32_t full = (1u << n) - 1u;
+    std::memset(out, 0, sizeof(*out));
+    out->phi = phi;
+    out->psi = psi;
+    out->n = (uint8_t)n;
+    out->cls = 0;
+    out->world = (uint8_t)w;
+    for (int v = 0; v < n; ++v) out->succ[v] = (uint32_t)((rel >> (v * n)) & full);
+    for (int i = 0; i < k; ++i) out->val[i] = (x >> (i * n)) & full;
+    return MK_OK;
+}

@@ -1,0 +1,164 @@
+"""Python driver over libmk: device buffers from PyTorch, kernels from libmk.
+
+``CensusJob`` and ``SeparateJob`` own the device memory of one batch
+(programs, sampled valuations, workspace, outputs, status word) and call the
+C ABI on the current torch CUDA stream.  Host-side steps are marshalling
+only: compiling texts (mk_compile), uploading, launching, downloading, and
+re-checking every reported witness with mk_certify.
+"""
+import numpy as np
+import torch
+
+from . import mk, workloads
+
+CLASSES = ("K", "T", "S4", "S5")
+
+
+def _stream_ptr(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _dev_bytes(arr, device):
+    """Upload a numpy array as a uint8 device tensor."""
+    t = torch.from_numpy(np.ascontiguousarray(arr).view(np.uint8).reshape(-1).copy())
+    return t.to(device)
+
+
+class CensusJob:
+    """One census batch: texts x classes x n in [n_min, n_max]."""
+
+    def __init__(self, texts=None, classes=CLASSES, n_min=1, n_max=5, samples=256, seed=2,
+                 device="cuda", tune=None, frame_lo=0, frame_hi=mk.NO_KEY, progs=None,
+                 sample_table=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("CensusJob needs a CUDA device (there is no CPU fallback)")
+        self.texts = list(texts) if texts is not None else None
+        self.progs = progs if progs is not None else mk.compile_batch(self.texts)
+        self.nprog = len(self.progs)
+        self.classes = tuple(c for c in CLASSES if c in classes)
+        self.n_min, self.n_max = n_min, n_max
+        self.S = samples
+        self.seed = seed
+        self.device = torch.device(device)
+        if samples:
+            self.sample_table = (sample_table if sample_table is not None
+                                 else workloads.valuation_table(seed, samples, n_max))
+        else:
+            self.sample_table = None
+        self.d_progs = _dev_bytes(self.progs, self.device)
+        self.d_samples = (_dev_bytes(self.sample_table, self.device) if samples else None)
+        depth = int(self.progs["depth"].max()) if self.nprog else 0
+        self.cfg = mk.census_cfg(self.classes, n_min, n_max, samples,
+                                 self.d_samples.data_ptr() if samples else 0, frame_lo, frame_hi, tune,
+                                 max_depth=max(depth, 1))
+        self.ws_bytes = mk.census_workspace_size(self.cfg, self.nprog)
+        if self.ws_bytes == 0:
+            raise mk.MkError(-5, "mk_census_workspace_size")
+        self.d_ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        self.nn = n_max - n_min + 1
+        self.d_out = torch.empty(self.nprog * len(self.classes) * self.nn * 3, dtype=torch.int64,
+                                 device=self.device)
+        self.d_status = torch.zeros(1, dtype=torch.int32, device=self.device)
+
+    def launch(self, stream=None):
+        """Enqueue the whole census on the stream (no synchronisation)."""
+        self.d_status.zero_()
+        mk.census_raw(self.d_progs.data_ptr(), self.nprog, self.cfg, self.d_out.data_ptr(),
+                      self.d_status.data_ptr(), self.d_ws.data_ptr(), self.ws_bytes, _stream_ptr(stream))
+
+    def check_status(self):
+        st = int(self.d_status.item())
+        if st:
+            raise mk.MkError(mk.status_error(st), "device status 0x%x" % st)
+
+    def results(self):
+        """uint64[nprog, ncls, nn, 3]: (cm_count, frames_refuted, witness_key)."""
+        torch.cuda.synchronize(self.device)
+        self.check_status()
+        out = self.d_out.cpu().numpy().view(np.uint64)
+        return out.reshape(self.nprog, len(self.classes), self.nn, 3)
+
+    def run(self):
+        self.launch()
+        return self.results()
+
+    def evals(self):
+        """Formula-frame-valuation evaluations in this census (algorithmic count)."""
+        total = 0
+        for p in self.progs:
+            k = int(p["nvars"])
+            for c in self.classes:
+                for n in range(self.n_min, self.n_max + 1):
+                    total += mk.class_frames(c, n) * n_valuations(k, n, self.S)
+        return total
+
+    def certificate(self, p, cls, n, key):
+        """mk_cert for the witness key of program p on layer (cls, n)."""
+        samples_n = self.sample_table[n] if self.S else None
+        return mk.witness_cert(mk.program_at(self.progs, p), self.texts[p], cls, n, self.S, samples_n, key)
+
+
+def n_valuations(k, n, S):
+    """Valuations per frame of a k-variable formula on layer n."""
+    if S == 0 or k <= 1 or (k * n < 32 and (1 << (k * n)) <= S):
+        return 1 << (k * n)
+    return S
+
+
+def lop3_per_eval(prog, n):
+    """Algorithmic logic ops per evaluation of the bit-sliced recurrence:
+    n per Boolean connective, n*n per modal operator, n for the refutation
+    test, all shared by 32 frames (one 32-bit word)."""
+    return (n * int(prog["n_bool"]) + n * n * int(prog["n_modal"]) + n) / 32.0
+
+
+class SeparateJob:
+    """Distinguishing-pair search for a list of (phi, psi) texts."""
+
+    def __init__(self, pairs, n_exh_min=1, n_exh_max=6, n_smp_min=0, n_smp_max=0, frames_per_n=0,
+                 seed=4, samples=0, device="cuda", tune=None, frame_lo=0, frame_hi=mk.NO_KEY):
+        if not torch.cuda.is_available():
+            raise RuntimeError("SeparateJob needs a CUDA device (there is no CPU fallback)")
+        self.pairs = list(pairs)
+        self.npairs = len(self.pairs)
+        self.pa = mk.compile_batch([a for a, _ in self.pairs])
+        self.pb = mk.compile_batch([b for _, b in self.pairs])
+        self.device = torch.device(device)
+        self.seed = seed
+        self.S = samples
+        self.sample_table = workloads.valuation_table(seed, samples, 8) if samples else None
+        self.d_pa = _dev_bytes(self.pa, self.device)
+        self.d_pb = _dev_bytes(self.pb, self.device)
+        self.d_samples = _dev_bytes(self.sample_table, self.device) if samples else None
+        self.cfg = mk.separate_cfg(n_exh_min, n_exh_max, n_smp_min, n_smp_max, samples,
+                                   self.d_samples.data_ptr() if samples else 0, frames_per_n, seed,
+                                   frame_lo, frame_hi, tune)
+        self.ws_bytes = mk.separate_workspace_size(self.cfg, self.npairs)
+        self.d_ws = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=self.device)
+        self.d_split = torch.empty(self.npairs, dtype=torch.int64, device=self.device)
+        self.d_status = torch.zeros(1, dtype=torch.int32, device=self.device)
+
+    def launch(self, stream=None):
+        self.d_status.zero_()
+        mk.separate_raw(self.d_pa.data_ptr(), self.d_pb.data_ptr(), self.npairs, self.cfg,
+                        self.d_split.data_ptr(), self.d_status.data_ptr(), self.d_ws.data_ptr(),
+                        self.ws_bytes, _stream_ptr(stream))
+
+    def results(self):
+        torch.cuda.synchronize(self.device)
+        st = int(self.d_status.item())
+        if st:
+            raise mk.MkError(mk.status_error(st), "device status 0x%x" % st)
+        return self.d_split.cpu().numpy().view(np.uint64)
+
+    def run(self):
+        self.launch()
+        return self.results()
+
+    def certificate(self, i, key):
+        n = int(key) >> 60
+        samples_n = self.sample_table[n] if self.S else None
+        a, b = self.pairs[i]
+        return mk.split_cert(mk.program_at(self.pa, i), mk.program_at(self.pb, i), a, b, self.seed,
+                             self.S, samples_n, int(key))

@@ -1,0 +1,315 @@
+"""Thin ctypes binding of libmk (include/mk.h): same names, marshalling only.
+
+Every step of the evaluation runs in libmk's kernels; this module packs
+arguments, lets PyTorch provide device memory and the current CUDA stream,
+and unpacks results.  There is no CPU fallback: if libmk.so is missing or
+no CUDA device is present, the device calls raise.
+"""
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmk.so")
+
+MK_MAX_CODE = 96
+MK_MAX_STACK = 4
+MK_MAX_VARS = 4
+MK_MAX_CERT_WORLDS = 32
+CLASS_BITS = {"K": 1, "T": 2, "S4": 4, "S5": 8}
+CLASS_NAMES = ("K", "T", "S4", "S5")
+NO_KEY = (1 << 64) - 1
+
+
+class MkError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, strerror(code) if _lib else "libmk", code))
+
+
+class mk_program(ctypes.Structure):
+    _fields_ = [("nodes", ctypes.c_uint16), ("n_instr", ctypes.c_uint8), ("nvars", ctypes.c_uint8),
+                ("modal_depth", ctypes.c_uint8), ("depth", ctypes.c_uint8),
+                ("n_modal", ctypes.c_uint8), ("n_bool", ctypes.c_uint8),
+                ("code", ctypes.c_uint8 * MK_MAX_CODE)]
+
+
+class mk_tune(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_uint16), ("tile", ctypes.c_uint16), ("words", ctypes.c_uint16),
+                ("persistent", ctypes.c_uint16)]
+
+
+class mk_census_cfg(ctypes.Structure):
+    _fields_ = [("classes", ctypes.c_uint32), ("n_min", ctypes.c_uint8), ("n_max", ctypes.c_uint8),
+                ("max_depth", ctypes.c_uint8), ("reserved", ctypes.c_uint8), ("samples", ctypes.c_uint32),
+                ("reserved2", ctypes.c_uint32), ("d_samples", ctypes.c_void_p),
+                ("frame_lo", ctypes.c_uint64), ("frame_hi", ctypes.c_uint64), ("tune", mk_tune)]
+
+
+class mk_result(ctypes.Structure):
+    _fields_ = [("cm_count", ctypes.c_uint64), ("frames_refuted", ctypes.c_uint64),
+                ("witness_key", ctypes.c_uint64)]
+
+
+class mk_cert(ctypes.Structure):
+    _fields_ = [("phi", ctypes.c_char_p), ("psi", ctypes.c_char_p), ("n", ctypes.c_uint8),
+                ("cls", ctypes.c_uint8), ("world", ctypes.c_uint8), ("reserved", ctypes.c_uint8),
+                ("succ", ctypes.c_uint32 * MK_MAX_CERT_WORLDS), ("val", ctypes.c_uint32 * MK_MAX_VARS)]
+
+
+class mk_separate_cfg(ctypes.Structure):
+    _fields_ = [("n_exh_min", ctypes.c_uint8), ("n_exh_max", ctypes.c_uint8),
+                ("n_smp_min", ctypes.c_uint8), ("n_smp_max", ctypes.c_uint8),
+                ("samples", ctypes.c_uint32), ("d_samples", ctypes.c_void_p),
+                ("frames_per_n", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+                ("frame_lo", ctypes.c_uint64), ("frame_hi", ctypes.c_uint64), ("tune", mk_tune)]
+
+
+PROGRAM_DTYPE = np.dtype([("nodes", "<u2"), ("n_instr", "u1"), ("nvars", "u1"), ("modal_depth", "u1"),
+                          ("depth", "u1"), ("n_modal", "u1"), ("n_bool", "u1"),
+                          ("code", "u1", (MK_MAX_CODE,))])
+assert PROGRAM_DTYPE.itemsize == ctypes.sizeof(mk_program) == 104
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGS = {
+    "mk_compile": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(mk_program), ctypes.POINTER(ctypes.c_int32)]),
+    "mk_compile_iff": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(mk_program),
+                                      ctypes.POINTER(ctypes.c_int32)]),
+    "mk_census_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(mk_census_cfg), ctypes.c_int32]),
+    "mk_census": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(mk_census_cfg),
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                 ctypes.c_void_p]),
+    "mk_class_frames": (ctypes.c_uint64, [ctypes.c_uint32, ctypes.c_int32]),
+    "mk_certify": (ctypes.c_int, [ctypes.POINTER(mk_cert)]),
+    "mk_witness_cert": (ctypes.c_int, [ctypes.POINTER(mk_program), ctypes.c_char_p, ctypes.c_uint32,
+                                       ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
+                                       ctypes.POINTER(mk_cert)]),
+    "mk_separate_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(mk_separate_cfg), ctypes.c_int32]),
+    "mk_separate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                   ctypes.POINTER(mk_separate_cfg), ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "mk_sample_relation": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint64]),
+    "mk_split_cert": (ctypes.c_int, [ctypes.POINTER(mk_program), ctypes.POINTER(mk_program), ctypes.c_char_p,
+                                     ctypes.c_char_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
+                                     ctypes.c_uint64, ctypes.POINTER(mk_cert)]),
+    "mk_census_launches": (ctypes.c_int32, [ctypes.POINTER(mk_census_cfg), ctypes.c_int32]),
+    "mk_calibrate_lop3": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32,
+                                         ctypes.c_uint32, ctypes.c_void_p]),
+    "mk_calibrate_ops_per_launch": (ctypes.c_uint64, [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32]),
+    "mk_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "mk_status_error": (ctypes.c_int, [ctypes.c_int32]),
+    "mk_version": (ctypes.c_int, []),
+}
+
+
+def lib():
+    """Load libmk.so (built by paper_2606_15437_gb300.build); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise OSError("libmk.so not built: run paper_2606_15437_gb300.build.build() "
+                              "(or __graft_entry__.build())")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def declared_symbols():
+    return list(_SIGS)
+
+
+def strerror(code):
+    return lib().mk_strerror(code).decode()
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise MkError(rc, what)
+
+
+# ------------------------------------------------------------ compile
+
+def compile(text):
+    """mk_compile: formula text -> mk_program."""
+    p = mk_program()
+    pos = ctypes.c_int32(-1)
+    rc = lib().mk_compile(text.encode(), ctypes.byref(p), ctypes.byref(pos))
+    if rc != 0:
+        raise MkError(rc, "mk_compile(%r) at %d" % (text, pos.value))
+    return p
+
+
+def compile_iff(phi, psi):
+    p = mk_program()
+    pos = ctypes.c_int32(-1)
+    _check(lib().mk_compile_iff(phi.encode(), psi.encode(), ctypes.byref(p), ctypes.byref(pos)),
+           "mk_compile_iff")
+    return p
+
+
+def compile_batch(texts):
+    """Compile many texts into a numpy array of PROGRAM_DTYPE records."""
+    out = np.zeros(len(texts), PROGRAM_DTYPE)
+    buf = out.view(np.uint8).reshape(len(texts), PROGRAM_DTYPE.itemsize)
+    for i, t in enumerate(texts):
+        p = compile(t)
+        buf[i] = np.frombuffer(bytes(p), np.uint8)
+    return out
+
+
+def program_at(progs, i):
+    return mk_program.from_buffer_copy(progs[i:i + 1].tobytes())
+
+
+# ------------------------------------------------------------- census
+
+def class_mask(classes):
+    m = 0
+    for c in classes:
+        m |= CLASS_BITS[c]
+    return m
+
+
+def census_cfg(classes, n_min, n_max, samples=0, d_samples=0, frame_lo=0, frame_hi=NO_KEY, tune=None,
+               max_depth=0):
+    cfg = mk_census_cfg()
+    cfg.max_depth = max_depth
+    cfg.classes = class_mask(classes) if not isinstance(classes, int) else classes
+    cfg.n_min, cfg.n_max = n_min, n_max
+    cfg.samples = samples
+    cfg.d_samples = d_samples or None
+    cfg.frame_lo, cfg.frame_hi = frame_lo, frame_hi
+    if tune:
+        for k, v in tune.items():
+            setattr(cfg.tune, k, v)
+    return cfg
+
+
+def census_workspace_size(cfg, nprog):
+    return int(lib().mk_census_workspace_size(ctypes.byref(cfg), nprog))
+
+
+def census_raw(d_progs, nprog, cfg, d_out, d_status, d_ws, ws_bytes, stream):
+    """mk_census on raw device pointers (ints) and a cudaStream_t (int)."""
+    _check(lib().mk_census(d_progs, nprog, ctypes.byref(cfg), d_out, d_status, d_ws, ws_bytes, stream),
+           "mk_census")
+
+
+def census_launches(cfg, nprog):
+    return int(lib().mk_census_launches(ctypes.byref(cfg), nprog))
+
+
+def calibrate_lop3(d_sink, blocks, threads, iters, seed, stream):
+    _check(lib().mk_calibrate_lop3(d_sink, blocks, threads, iters, seed, stream), "mk_calibrate_lop3")
+    return int(lib().mk_calibrate_ops_per_launch(blocks, threads, iters))
+
+
+def class_frames(cls, n):
+    return int(lib().mk_class_frames(CLASS_BITS[cls] if isinstance(cls, str) else cls, n))
+
+
+def status_error(status):
+    return int(lib().mk_status_error(int(status)))
+
+
+def decode_key(key):
+    """Census witness key -> (frame, valuation index or slot, world)."""
+    if key == NO_KEY:
+        return None
+    return (key >> 27, (key >> 3) & 0xFFFFFF, key & 7)
+
+
+def decode_split(key):
+    """Separation key -> (n, frame or sample, valuation, world)."""
+    if key == NO_KEY:
+        return None
+    return (key >> 60, (key >> 24) & ((1 << 36) - 1), (key >> 3) & ((1 << 21) - 1), key & 7)
+
+
+# ------------------------------------------------------- certificates
+
+def certify(phi, n, succ, val=(), world=0, cls=0, psi=None):
+    """mk_certify on an explicit certificate; returns 1 / 0 (or raises)."""
+    c = mk_cert()
+    c.phi = phi.encode()
+    c.psi = psi.encode() if psi is not None else None
+    c.n, c.cls, c.world = n, (CLASS_NAMES.index(cls) if isinstance(cls, str) else cls), world
+    for i, s in enumerate(succ):
+        c.succ[i] = s
+    for i, v in enumerate(val):
+        c.val[i] = v
+    rc = lib().mk_certify(ctypes.byref(c))
+    if rc < 0:
+        raise MkError(rc, "mk_certify")
+    return rc
+
+
+def certify_struct(c):
+    return lib().mk_certify(ctypes.byref(c))
+
+
+def witness_cert(prog, phi, cls, n, samples, h_samples_n, key):
+    c = mk_cert()
+    keep = None
+    ptr = None
+    if h_samples_n is not None:
+        keep = np.ascontiguousarray(np.asarray(h_samples_n, np.uint32))
+        ptr = keep.ctypes.data_as(ctypes.c_void_p)
+    phi_b = phi.encode()
+    _check(lib().mk_witness_cert(ctypes.byref(prog), phi_b, CLASS_BITS[cls], n, samples, ptr, key,
+                                 ctypes.byref(c)), "mk_witness_cert")
+    c._keep = (phi_b, keep)
+    return c
+
+
+def split_cert(prog_a, prog_b, phi, psi, seed, samples, h_samples_n, key):
+    c = mk_cert()
+    keep = None
+    ptr = None
+    if h_samples_n is not None:
+        keep = np.ascontiguousarray(np.asarray(h_samples_n, np.uint32))
+        ptr = keep.ctypes.data_as(ctypes.c_void_p)
+    a, b = phi.encode(), psi.encode()
+    _check(lib().mk_split_cert(ctypes.byref(prog_a), ctypes.byref(prog_b), a, b, seed, samples, ptr, key,
+                               ctypes.byref(c)), "mk_split_cert")
+    c._keep = (a, b, keep)
+    return c
+
+
+def sample_relation(seed, n, s):
+    return int(lib().mk_sample_relation(seed, n, s))
+
+
+# --------------------------------------------------------- separation
+
+def separate_cfg(n_exh_min=1, n_exh_max=6, n_smp_min=0, n_smp_max=0, samples=0, d_samples=0,
+                 frames_per_n=0, seed=0, frame_lo=0, frame_hi=NO_KEY, tune=None):
+    cfg = mk_separate_cfg()
+    cfg.n_exh_min, cfg.n_exh_max = n_exh_min, n_exh_max
+    cfg.n_smp_min, cfg.n_smp_max = n_smp_min, n_smp_max
+    cfg.samples = samples
+    cfg.d_samples = d_samples or None
+    cfg.frames_per_n, cfg.seed = frames_per_n, seed
+    cfg.frame_lo, cfg.frame_hi = frame_lo, frame_hi
+    if tune:
+        for k, v in tune.items():
+            setattr(cfg.tune, k, v)
+    return cfg
+
+
+def separate_raw(d_phi, d_psi, npairs, cfg, d_split, d_status, d_ws, ws_bytes, stream):
+    _check(lib().mk_separate(d_phi, d_psi, npairs, ctypes.byref(cfg), d_split, d_status, d_ws, ws_bytes,
+                             stream), "mk_separate")
+
+
+def separate_workspace_size(cfg, npairs):
+    return int(lib().mk_separate_workspace_size(ctypes.byref(cfg), npairs))

@@ -1,0 +1,185 @@
+"""GPU parity of mk_census against the CPU oracle (bit-exact).
+
+Every count, refuted-frame count and witness key is compared element by
+element with oracle.census on the same seeded inputs; every witness is
+re-checked by mk_certify.  Sizes: the PR1 configuration in full (n <= 3),
+random formulas through n = 4 with sampled valuations, five-world layers on
+K-index windows, closed forms on full five-world layers, and the
+five-world census batch in the launch configuration bench.py times, checked
+on sampled outputs.
+"""
+import math
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_15437_gb300 import build as mkbuild
+from paper_2606_15437_gb300 import mk
+from paper_2606_15437_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CLS = ("K", "T", "S4", "S5")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    mkbuild.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def engine():
+    from paper_2606_15437_gb300 import engine as E
+    return E
+
+
+def oracle_key(r):
+    if r["witness"] is None:
+        return mk.NO_KEY
+    f, v, w = r["witness"]
+    return (f << 27) | (v << 3) | w
+
+
+def check_against_oracle(job, res, texts, n_values, classes=CLS, certify=True, **rng):
+    for p, text in enumerate(texts):
+        for ci, c in enumerate(job.classes):
+            if c not in classes:
+                continue
+            for n in n_values:
+                ni = n - job.n_min
+                samples = job.sample_table[n] if job.S else None
+                want = oracle.census(text, c, n, samples=samples, **rng)
+                got = tuple(int(x) for x in res[p, ci, ni])
+                assert got == (want["cm_count"], want["frames_refuted"], oracle_key(want)), (text, c, n)
+                if certify and got[2] != mk.NO_KEY:
+                    cert = job.certificate(p, c, n, got[2])
+                    assert mk.certify_struct(cert) == 1, (text, c, n)
+
+
+def test_pr1_config_full():
+    texts = W.pr1_formulas()
+    job = engine().CensusJob(texts, CLS, 1, 3, samples=0)
+    res = job.run()
+    check_against_oracle(job, res, texts, (1, 2, 3))
+
+
+@pytest.mark.parametrize("tile,block", [(1, 128), (7, 256), (16, 256), (64, 128)])
+def test_random_formulas_sampled_valuations(tile, block):
+    rng = random.Random(tile)
+    texts = [W.random_formula(rng, rng.randint(1, 20), rng.randint(0, 4), rng.randint(0, 4))
+             for _ in range(37)]
+    job = engine().CensusJob(texts, CLS, 1, 4, samples=16, seed=tile,
+                             tune={"tile": tile, "block": block})
+    res = job.run()
+    check_against_oracle(job, res, texts, (1, 2, 3))
+    # n = 4 on a subset (the oracle pays 2^16 frames each)
+    check_against_oracle(job, res, texts[:6], (4,))
+
+
+def test_long_formulas_many_registers():
+    rng = random.Random(99)
+    texts = []
+    while len(texts) < 12:
+        t = W.random_formula(rng, rng.randint(40, 64), rng.randint(1, 8), rng.randint(0, 2))
+        if mk.compile(t).depth >= 2:
+            texts.append(t)
+    t = "p"
+    for _ in range(5):
+        t = "(%s & %s)" % (t, t.replace("p", "q"))
+    texts.append(t)
+    job = engine().CensusJob(texts, CLS, 1, 3, samples=0)
+    check_against_oracle(job, job.run(), texts, (1, 2, 3))
+
+
+def test_five_world_windows():
+    # K and T layers at n = 5 restricted to K-index windows; the oracle
+    # computes the same windows
+    rng = random.Random(5)
+    texts = [W.random_formula(rng, rng.randint(3, 24), rng.randint(1, 4), rng.randint(0, 3))
+             for _ in range(10)] + list(W.AXIOMS)
+    for lo in (0, 123457, 2 ** 25 - 5000):
+        hi = lo + 5000
+        job = engine().CensusJob(texts, ("K", "T", "S4"), 5, 5, samples=256, seed=2,
+                                 frame_lo=lo, frame_hi=hi)
+        check_against_oracle(job, job.run(), texts, (5,), f_lo=lo, f_hi=hi)
+
+
+def _t_axiom(n):
+    valid = sum(math.comb(n, s) * (2 ** n) ** s * (2 ** n - 2 ** s) ** (n - s) for s in range(n + 1))
+    return 2 ** (n * n) * 2 ** n - valid
+
+
+def test_closed_forms_full_five_worlds():
+    texts = [W.T_AXIOM, W.FOUR_AXIOM, "<>T", "[]F", "p -> []<>p", W.K_AXIOM, "F"]
+    job = engine().CensusJob(texts, CLS, 1, 5, samples=256)
+    res = job.run()
+    K, T, S4, S5 = 0, 1, 2, 3
+    for n in range(1, 6):
+        i = n - 1
+        assert int(res[0, K, i, 0]) == _t_axiom(n)
+        assert int(res[0, K, i, 1]) == 2 ** (n * n) - 2 ** (n * n - n)
+        assert int(res[0, T, i, 0]) == int(res[0, S4, i, 0]) == int(res[0, S5, i, 0]) == 0
+        transitive = [2, 13, 171, 3994, 154303][i]           # OEIS A006905
+        assert int(res[1, K, i, 1]) == 2 ** (n * n) - transitive
+        assert int(res[1, S4, i, 0]) == int(res[1, S5, i, 0]) == 0
+        assert int(res[2, K, i, 1]) == 2 ** (n * n) - (2 ** n - 1) ** n
+        assert int(res[3, K, i, 1]) == 2 ** (n * n) - 1
+        assert int(res[4, K, i, 1]) == 2 ** (n * n) - 2 ** (n * (n + 1) // 2)
+        assert int(res[5, :, i, 0].sum()) == 0 and int(res[5, K, i, 2]) == mk.NO_KEY
+        sizes = [2 ** (n * n), 2 ** (n * n - n), [1, 4, 29, 355, 6942][i], [1, 2, 5, 15, 52][i]]
+        assert [int(res[6, c, i, 1]) for c in range(4)] == sizes
+    assert int(res[0, K, 0, 2]) == 0     # witness (frame 0, valuation 0, world 0)
+
+
+def test_bench_workload_sampled_outputs():
+    """The five-world census batch as bench.py launches it (5,624 formulas,
+    K/T/S4/S5, n <= 5, S = 256), checked on sampled outputs: every sampled
+    witness is certified and minimal (oracle scan of the frames before it),
+    and all counts of sampled formulas at n <= 3 equal the oracle's."""
+    texts = W.census5_formulas()
+    job = engine().CensusJob(texts, CLS, 1, 5, samples=256, seed=2)
+    res = job.run()
+    rng = random.Random(0)
+    picks = rng.sample(range(len(texts)), 24) + [len(texts) - 3, len(texts) - 2, len(texts) - 1]
+    for p in picks:
+        text = texts[p]
+        for ci, c in enumerate(CLS):
+            for n in (1, 2, 3):
+                samples = job.sample_table[n]
+                want = oracle.census(text, c, n, samples=samples)
+                got = tuple(int(x) for x in res[p, ci, n - 1])
+                assert got == (want["cm_count"], want["frames_refuted"], oracle_key(want)), (text, c, n)
+            for n in (4, 5):
+                key = int(res[p, ci, n - 1, 2])
+                if key == mk.NO_KEY:
+                    assert int(res[p, ci, n - 1, 0]) == 0
+                    continue
+                cert = job.certificate(p, c, n, key)
+                assert mk.certify_struct(cert) == 1
+                f = key >> 27
+                if f < 200000:
+                    # no earlier frame refutes it, and this frame's witness matches
+                    want = oracle.census(text, c, n, samples=job.sample_table[n], f_lo=0, f_hi=f + 1)
+                    assert oracle_key(want) == key, (text, c, n)
+
+
+def test_empty_and_ragged_batches():
+    E = engine()
+    job = E.CensusJob([], CLS, 1, 2, samples=0, progs=np.zeros(0, mk.PROGRAM_DTYPE))
+    assert job.run().shape == (0, 4, 2, 3)
+    texts = W.pr1_formulas()[:17]
+    job = E.CensusJob(texts, ("S5",), 3, 3, samples=0, tune={"tile": 16})
+    check_against_oracle(job, job.run(), texts, (3,))
+
+
+def test_malformed_program_sets_status():
+    E = engine()
+    progs = mk.compile_batch(["p", "q"])
+    progs["code"][1][0] = 250          # not an instruction
+    job = E.CensusJob(["p", "q"], ("K",), 1, 2, samples=0, progs=progs)
+    with pytest.raises(mk.MkError) as e:
+        job.run()
+    assert e.value.code == -8

@@ -1,0 +1,213 @@
+"""CPU tests of libmk's host side: the ABI exports, mk_compile, mk_certify.
+
+No GPU and no compute kernel is called here.  The compiled programs are
+checked by interpreting their instruction set (as mk.h defines it) in plain
+Python over explicit truth sets and comparing with the oracle on small
+frames, so register allocation and constant folding are covered on CPU.
+"""
+import os
+import random
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import pyref
+from paper_2606_15437_gb300 import build as mkbuild
+from paper_2606_15437_gb300 import mk
+from paper_2606_15437_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    mkbuild.build()
+
+
+def test_exports_every_declared_symbol():
+    header = open(os.path.join(ROOT, "include", "mk.h")).read()
+    declared = set(re.findall(r"^\s*(?:[\w\s\*]+?)\b(mk_\w+)\s*\(", header, re.M))
+    assert {"mk_compile", "mk_census", "mk_separate", "mk_certify"} <= declared
+    L = mk.lib()
+    for name in sorted(declared):
+        assert hasattr(L, name), name
+    assert set(mk.declared_symbols()) <= declared
+    assert mk.lib().mk_version() == 1
+
+
+def test_struct_sizes():
+    import ctypes
+    assert ctypes.sizeof(mk.mk_program) == 104
+    assert ctypes.sizeof(mk.mk_census_cfg) == 48
+    assert ctypes.sizeof(mk.mk_result) == 24
+
+
+# ------------------------------------------------------ program semantics
+
+def run_program(prog, n, R, V):
+    """Interpret a compiled program (mk.h's accumulator machine) over
+    explicit truth sets (sets of worlds)."""
+    full = set(range(n))
+    succ = [{v for v in range(n) if R[w][v]} for w in range(n)]
+    atom = [{w for w in range(n) if V[i][w]} for i in range(mk.MK_MAX_VARS)]
+    A, st = set(), [None] * mk.MK_MAX_STACK
+    for c in list(prog.code)[:prog.n_instr]:
+        op, arg = c & 15, c >> 4
+        if op == 0:
+            A = set(atom[arg])
+        elif op == 1:
+            A = set(full)
+        elif op == 2:
+            A = set()
+        elif op == 3:
+            A = full - A
+        elif op == 4:
+            A = {w for w in full if succ[w] <= A}
+        elif op == 5:
+            A = {w for w in full if succ[w] & A}
+        elif op == 6:
+            st[arg] = set(A)
+        elif 7 <= op <= 11:
+            S = st[arg]
+            A = [S & A, S | A, (full - S) | A, (full - A) | S, full - (S ^ A)][op - 7]
+        else:
+            a = atom[arg]
+            A = [A & a, A | a, (full - A) | a, (full - a) | A][op - 12]
+    return A
+
+
+def _texts(seed, count, maxlen=14):
+    rng = random.Random(seed)
+    return [W.random_formula(rng, rng.randint(1, maxlen), rng.randint(0, 4), rng.randint(0, 3))
+            for _ in range(count)]
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_compiled_programs_match_oracle(seed):
+    rng = np.random.default_rng(seed)
+    for text in _texts(seed, 60) + list(W.AXIOMS) + [W.alpha(3), "T", "F", "~T", "p <-> []p"]:
+        prog = mk.compile(text)
+        k = prog.nvars
+        for _ in range(6):
+            n = int(rng.integers(1, 5))
+            R = rng.integers(0, 2, (n, n)).astype(np.uint8)
+            V = rng.integers(0, 2, (4, n)).astype(np.uint8)
+            got = run_program(prog, n, R, V)
+            want = oracle.eval_model(text, R, V)
+            assert got == {w for w in range(n) if want[w]}, text
+        assert prog.nvars == oracle.nvars(text)
+        assert prog.nodes == W.nodes(text) or "<->" in text
+
+
+def test_compile_iff_is_biconditional():
+    prog = mk.compile_iff(W.alpha(2), W.alpha(3))
+    R = np.zeros((6, 6), np.uint8)
+    for w in range(5):
+        R[w, w + 1] = 1
+    got = run_program(prog, 6, R, np.zeros((4, 6), np.uint8))
+    a, b = oracle.eval_model(W.alpha(2), R), oracle.eval_model(W.alpha(3), R)
+    assert got == {w for w in range(6) if a[w] == b[w]}
+
+
+def test_register_bound_for_64_nodes():
+    rng = random.Random(7)
+    worst = 0
+    for _ in range(500):
+        t = W.random_formula(rng, 64, rng.randint(1, 8), rng.randint(0, 4))
+        p = mk.compile(t)
+        worst = max(worst, p.depth)
+        assert p.depth <= mk.MK_MAX_STACK and p.n_instr <= mk.MK_MAX_CODE
+    # a complete binary tree of 32 atoms (63 nodes) needs the deepest stack
+    t = "p"
+    for d in range(5):
+        t = "(%s & %s)" % (t, t.replace("p", "q"))
+    assert mk.compile(t).depth == mk.MK_MAX_STACK
+
+
+@pytest.mark.parametrize("bad,code", [("p &", -1), ("(p", -1), ("p4", -3), ("x", -1), ("p & & q", -1),
+                                      ("[]" * 70 + "p", -2)])
+def test_compile_errors(bad, code):
+    with pytest.raises(mk.MkError) as e:
+        mk.compile(bad)
+    assert e.value.code == code
+
+
+def test_precedence_and_associativity():
+    # -> is right associative and binds loosest; & binds tighter than |
+    for a, b in [("p -> q -> r", "p -> (q -> r)"), ("p | q & r", "p | (q & r)"),
+                 ("~p & q", "(~p) & q"), ("[]p -> q", "([]p) -> q"), ("p & q -> r | s", "(p & q) -> (r | s)")]:
+        pa, pb = mk.compile(a), mk.compile(b)
+        for f in range(64):
+            R = oracle.frame_matrix(f % 16, 2)
+            V = np.array([[(f >> (i * 2 + w)) & 1 for w in range(2)] for i in range(4)], np.uint8)
+            assert run_program(pa, 2, R, V) == run_program(pb, 2, R, V), (a, b)
+
+
+# ------------------------------------------------------------ certify
+
+def test_certify_paper_certificate():
+    succ = [2, 4, 8, 16, 32, 0]
+    assert mk.certify(W.alpha(3), 6, succ, world=0) == 1       # alpha_3 false at w0
+    assert mk.certify(W.alpha(2), 6, succ, world=0) == 0       # alpha_2 true there
+    assert mk.certify(W.alpha(2), 6, succ, world=0, psi=W.alpha(3)) == 1
+    assert mk.certify(W.alpha(2), 6, succ, world=1, psi=W.alpha(3)) == 0
+
+
+def test_certify_checks_class():
+    # T axiom countermodel on the one-world irreflexive frame is valid in K
+    # but the frame is not in T
+    assert mk.certify("[]p -> p", 1, [0], [0], 0, cls="K") == 1
+    assert mk.certify("[]p -> p", 1, [0], [0], 0, cls="T") == 0
+    # a non-transitive reflexive frame is not S4
+    assert mk.certify("[]p -> [][]p", 3, [0b011, 0b110, 0b100], [0b011], 0, cls="T") == 1
+    assert mk.certify("[]p -> [][]p", 3, [0b011, 0b110, 0b100], [0b011], 0, cls="S4") == 0
+
+
+def test_certify_rejects_malformed():
+    with pytest.raises(mk.MkError):
+        mk.certify("p &", 2, [0, 0])
+    with pytest.raises(mk.MkError):
+        mk.certify("p", 2, [4, 0])          # successor outside the frame
+    with pytest.raises(mk.MkError):
+        mk.certify("p", 2, [0, 0], world=3)
+
+
+def test_certify_agrees_with_oracle_on_random_models():
+    rng = np.random.default_rng(3)
+    for text in _texts(9, 80):
+        n = int(rng.integers(1, 6))
+        R = rng.integers(0, 2, (n, n)).astype(np.uint8)
+        V = rng.integers(0, 2, (4, n)).astype(np.uint8)
+        succ = [int(sum(int(R[w, v]) << v for v in range(n))) for w in range(n)]
+        val = [int(sum(int(V[i, w]) << w for w in range(n))) for i in range(4)]
+        truth = oracle.eval_model(text, R, V)
+        for w in range(n):
+            assert mk.certify(text, n, succ, val, w) == (0 if truth[w] else 1), text
+
+
+def test_certify_long_path_lemma8():
+    for m in (1, 2, 3, 5, 10):
+        L = 2 * m + 2
+        succ = [1 << (w + 1) for w in range(L - 1)] + [0]
+        assert mk.certify(W.alpha(m), L, succ, world=0, psi=W.alpha(m + 1)) == 1
+
+
+def test_sample_relation_matches_oracle_generator():
+    for n in (7, 8):
+        for s in (0, 1, 2, 1000, 123456789):
+            assert mk.sample_relation(42, n, s) == oracle.sample_frame(42, n, s)
+
+
+def test_class_frames():
+    assert [mk.class_frames("S4", n) for n in range(1, 7)] == [1, 4, 29, 355, 6942, 209527]
+    assert [mk.class_frames("S5", n) for n in range(1, 7)] == [1, 2, 5, 15, 52, 203]
+    assert mk.class_frames("T", 5) == 2 ** 20 and mk.class_frames("K", 6) == 2 ** 36
+
+
+def test_witness_cert_decoding():
+    prog = mk.compile("[]p -> p")
+    key = (0 << 27) | (0 << 3) | 0
+    c = mk.witness_cert(prog, "[]p -> p", "K", 1, 0, None, key)
+    assert c.n == 1 and c.succ[0] == 0 and c.val[0] == 0 and mk.certify_struct(c) == 1
