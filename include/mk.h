@@ -125,7 +125,9 @@ int mk_compile_iff(const char *phi, const char *psi, mk_program *out, int32_t *e
 typedef struct {
     uint16_t block;        /* threads per CTA: 128, 256 or 512 (0 = 256)    */
     uint16_t tile;         /* formulas per CTA, 1..64 (0 = 16)              */
-    uint16_t words;        /* 32-frame words per thread, 1..8 (0 = 1)       */
+    uint16_t units;        /* units per dispatched instruction: valuations  */
+                           /* (census: 2, 4 or 8; 0 = 8) -- the same program */
+                           /* step is applied to that many units at once      */
     uint16_t persistent;   /* 1 = one persistent launch over a work queue   */
 } mk_tune;
 

@@ -31,7 +31,7 @@ namespace mkd {
 
 constexpr int SRC_K = 0, SRC_T = 1, SRC_LIST = 2;
 constexpr int ROW_CAP = 128;          // atom rows staged at a time
-constexpr int CENSUS_U = 2;           // valuations per dispatched instruction
+constexpr int OPS_STRIDE = MK_MAX_CODE + 2;   // decoded ops per program (END + prefetch pad)
 
 struct LayerArgs {
     const mk_program *progs;
@@ -55,9 +55,10 @@ struct LayerArgs {
 // Shared memory of one census CTA.
 template <int N, int U, int BLOCK>
 struct CensusSmem {
-    static constexpr size_t code_bytes(int tile) { return ((size_t)tile * MK_MAX_CODE + 16 + 15) & ~(size_t)15; }
+    static constexpr size_t code_bytes(int tile) { return ((size_t)tile * OPS_STRIDE * 3 + 15) & ~(size_t)15; }
     static constexpr size_t meta_bytes(int tile) { return (size_t)tile * 32; }   // 2 int + 3 u64
-    static constexpr size_t row_bytes() { return (size_t)ROW_CAP * RowShape<N>::WORDS * 4; }
+    // ROW_CAP rows plus U rows of slack read (and masked) by a partial last step
+    static constexpr size_t row_bytes() { return (size_t)(ROW_CAP + U) * RowShape<N>::WORDS * 4; }
     static constexpr size_t stack_bytes(int depth) { return (size_t)depth * U * N * BLOCK * 4; }
     static size_t total(int tile, int depth) {
         return code_bytes(tile) + meta_bytes(tile) + row_bytes() + stack_bytes(depth);
@@ -120,7 +121,8 @@ __global__ void __launch_bounds__(BLOCK) census_layer_kernel(LayerArgs a) {
     constexpr int RW = RowShape<N>::WORDS;
     extern __shared__ __align__(16) uint8_t smem[];
     const int tile = a.tile;
-    uint8_t *s_code = smem;
+    uint16_t *s_offs = (uint16_t *)smem;
+    uint8_t *s_ops = smem + (size_t)tile * OPS_STRIDE * 2;
     int *s_nin = (int *)(smem + SM::code_bytes(tile));
     int *s_k = s_nin + tile;
     unsigned long long *s_cm = (unsigned long long *)(s_k + tile);
@@ -150,12 +152,8 @@ __global__ void __launch_bounds__(BLOCK) census_layer_kernel(LayerArgs a) {
         s_cm[i] = 0;
         s_rf[i] = 0;
         s_key[i] = ~0ull;
+        if (nin >= 0) decode_program<N, U, BLOCK>(p, s_ops + i * OPS_STRIDE, s_offs + i * OPS_STRIDE);
     }
-    for (int i = threadIdx.x; i < np * MK_MAX_CODE / 4; i += BLOCK) {
-        const int pi = i / (MK_MAX_CODE / 4), wi = i % (MK_MAX_CODE / 4);
-        ((uint32_t *)s_code)[i] = ((const uint32_t *)a.progs[p0 + pi].code)[wi];
-    }
-    if (threadIdx.x < 4) ((uint32_t *)(s_code + (size_t)np * MK_MAX_CODE))[threadIdx.x] = 0;
 
     uint64_t nframes = a.nframes;
     if (a.src == SRC_LIST) {
@@ -181,7 +179,8 @@ __global__ void __launch_bounds__(BLOCK) census_layer_kernel(LayerArgs a) {
         const int k = s_k[fi];
         const bool exh = exhaustive_vals(k, N, a.S);
         const uint32_t nval = exh ? (1u << (k * N)) : a.S;
-        const uint8_t *code = s_code + fi * MK_MAX_CODE;
+        const uint8_t *ops = s_ops + fi * OPS_STRIDE;
+        const uint16_t *offs = s_offs + fi * OPS_STRIDE;
         uint32_t cnt = 0, rf = 0, best_j = 0;
         int best_l = 32, best_w = 0;
         for (uint32_t c0 = 0; c0 < nval; c0 += ROW_CAP) {
@@ -196,23 +195,38 @@ __global__ void __launch_bounds__(BLOCK) census_layer_kernel(LayerArgs a) {
                 rows_kind = exh ? 0 : 1;
                 rows_c0 = c0;
             }
-            for (uint32_t jj = 0; jj < cn; jj += U) {
-                const uint32_t *rows[U];
+            // valid lanes per unit: all lanes of the frame word, except the
+            // units past the chunk's end in its last step
+            uint32_t vm[U];
 #pragma unroll
-                for (int u = 0; u < U; ++u) rows[u] = s_rows + min(jj + u, cn - 1) * RW;
+            for (int u = 0; u < U; ++u) vm[u] = valid;
+            for (uint32_t jj = 0; jj < cn; jj += U) {
+                if (jj + U > cn) {
+#pragma unroll
+                    for (int u = 0; u < U; ++u) vm[u] = (jj + u < cn) ? valid : 0u;
+                }
                 uint32_t A[U][N];
-                run_program<N, U, 1, BLOCK>(code, nin, rows, E, s_stack, A);
+                run_program<N, U, 1, BLOCK, RW>(ops, offs, s_rows + jj * RW, E, s_stack, A);
+                uint32_t bad[U], any = 0;
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     uint32_t all = A[u][0];
 #pragma unroll
                     for (int w = 1; w < N; ++w) all &= A[u][w];
-                    const uint32_t bad = (jj + u < cn) ? (~all & valid) : 0u;
-                    if (bad) {
-                        cnt += __popc(bad);
-                        rf |= bad;
-                        const int l = __ffs(bad) - 1;
-                        if (l < best_l) {
+                    bad[u] = ~all & vm[u];
+                    cnt += __popc(bad[u]);
+                    any |= bad[u];
+                }
+                rf |= any;
+                // a lane below the best so far: its first refuting valuation is
+                // the first unit (in valuation order) that refutes it
+                uint32_t lowmask = (best_l < 32 ? (1u << best_l) : 0u) - 1u;
+                if (any & lowmask) {
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const uint32_t lower = bad[u] & lowmask;
+                        if (lower) {
+                            const int l = __ffs(lower) - 1;
                             best_l = l;
                             best_j = c0 + jj + u;
                             int bw = 0;
@@ -220,6 +234,7 @@ __global__ void __launch_bounds__(BLOCK) census_layer_kernel(LayerArgs a) {
                             for (int w = N - 1; w >= 0; --w)
                                 if (!((A[u][w] >> l) & 1u)) bw = w;
                             best_w = bw;
+                            lowmask = (1u << l) - 1u;
                         }
                     }
                 }
@@ -405,34 +420,42 @@ int check_cfg(const mk_census_cfg *cfg, int32_t nprog) {
     if (t.block && t.block != 128 && t.block != 256) return MK_E_ARG;
     if (t.tile > 64) return MK_E_ARG;
     if (cfg->max_depth > MK_MAX_STACK) return MK_E_ARG;
+    if (t.units && t.units != 2 && t.units != 4 && t.units != 8) return MK_E_ARG;
     return MK_OK;
 }
 
-template <int N, int BLOCK>
+template <int N, int U, int BLOCK>
 void launch_layer_b(const LayerArgs &a, cudaStream_t s) {
     const uint64_t words = a.word_hi > a.word_lo ? a.word_hi - a.word_lo : 0;
     if (words == 0 || a.nprog == 0) return;
     dim3 grid((unsigned)((words + BLOCK - 1) / BLOCK), (unsigned)((a.nprog + a.tile - 1) / a.tile));
-    const size_t sm = CensusSmem<N, CENSUS_U, BLOCK>::total(a.tile, a.depth);
-    auto kern = census_layer_kernel<N, CENSUS_U, BLOCK>;
+    const size_t sm = CensusSmem<N, U, BLOCK>::total(a.tile, a.depth);
+    auto kern = census_layer_kernel<N, U, BLOCK>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kern<<<grid, BLOCK, sm, s>>>(a);
 }
 
-template <int N>
-void launch_layer(const LayerArgs &a, int block, cudaStream_t s) {
-    if (block == 128) launch_layer_b<N, 128>(a, s);
-    else launch_layer_b<N, 256>(a, s);
+template <int N, int U>
+void launch_layer_u(const LayerArgs &a, int block, cudaStream_t s) {
+    if (block == 128) launch_layer_b<N, U, 128>(a, s);
+    else launch_layer_b<N, U, 256>(a, s);
 }
 
-void launch_layer_n(int n, const LayerArgs &a, int block, cudaStream_t s) {
+template <int N>
+void launch_layer(const LayerArgs &a, int block, int units, cudaStream_t s) {
+    if (units == 2) launch_layer_u<N, 2>(a, block, s);
+    else if (units == 8) launch_layer_u<N, 8>(a, block, s);
+    else launch_layer_u<N, 4>(a, block, s);
+}
+
+void launch_layer_n(int n, const LayerArgs &a, int block, int units, cudaStream_t s) {
     switch (n) {
-    case 1: launch_layer<1>(a, block, s); break;
-    case 2: launch_layer<2>(a, block, s); break;
-    case 3: launch_layer<3>(a, block, s); break;
-    case 4: launch_layer<4>(a, block, s); break;
-    case 5: launch_layer<5>(a, block, s); break;
-    case 6: launch_layer<6>(a, block, s); break;
+    case 1: launch_layer<1>(a, block, units, s); break;
+    case 2: launch_layer<2>(a, block, units, s); break;
+    case 3: launch_layer<3>(a, block, units, s); break;
+    case 4: launch_layer<4>(a, block, units, s); break;
+    case 5: launch_layer<5>(a, block, units, s); break;
+    case 6: launch_layer<6>(a, block, units, s); break;
     }
 }
 
@@ -518,6 +541,7 @@ extern "C" int mk_census(const mk_program *d_progs, int32_t nprog, const mk_cens
     const int block = cfg->tune.block ? cfg->tune.block : 256;
     const int tile = cfg->tune.tile ? cfg->tune.tile : 16;
     const int depth = cfg->max_depth ? cfg->max_depth : MK_MAX_STACK;
+    const int units = cfg->tune.units ? cfg->tune.units : 8;
 
     // class lists for S4 / S5
     for (int c = 0; c < 2; ++c) {
@@ -567,7 +591,7 @@ extern "C" int mk_census(const mk_program *d_progs, int32_t nprog, const mk_cens
                 a.word_lo = 0;
                 a.word_hi = (a.nframes + 31) / 32;
             }
-            launch_layer_n(n, a, block, s);
+            launch_layer_n(n, a, block, units, s);
         }
         ++ci;
     }

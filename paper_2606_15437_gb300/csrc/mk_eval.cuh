@@ -1,6 +1,5 @@
 // mk_eval.cuh -- device building blocks shared by the census and the
-// separation kernels: bit-sliced frames and the register-resident postfix
-// interpreter.
+// separation kernels: bit-sliced frames and the postfix interpreter.
 //
 // Layout ("frame word"): one 32-bit register word holds one bit for each of
 // 32 consecutive frames, lane l <-> frame base + l.  A truth set of an
@@ -111,6 +110,14 @@ __device__ __forceinline__ uint32_t preorder_mask(const uint32_t (&E)[N * N], bo
 // the stack lives in shared memory, one column per thread (element (d, u,
 // w) at stack[((d*U + u)*N + w) * BLOCK], bank-conflict free); atom truth
 // sets come from shared-memory rows (see atom_row_word).
+//
+// Programs are pre-decoded when a CTA stages them (decode_program): one
+// byte per instruction holding the op (MK_OP_END after the last one) and a
+// 16-bit word offset holding the operand already scaled (stack entry d ->
+// d * U*N*BLOCK, variable i -> i * RS), so dispatch is a table jump with no
+// decoding arithmetic.
+
+constexpr int MK_OP_END = MK_NUM_OPS;
 
 // Words per variable in an atom row (a multiple of 4 for 16-byte loads).
 template <int N>
@@ -128,10 +135,23 @@ __device__ __forceinline__ uint32_t atom_row_word(uint32_t val, int idx) {
     return w < N ? 0u - ((val >> (i * N + w)) & 1u) : 0u;
 }
 
+// Decode program p into ops[0..n] (ops[n] = END) and offs[0..n).
+template <int N, int U, int BLOCK>
+__device__ __forceinline__ void decode_program(const mk_program &p, uint8_t *ops, uint16_t *offs) {
+    for (int i = 0; i < p.n_instr; ++i) {
+        const int op = p.code[i] & 15, arg = p.code[i] >> 4;
+        ops[i] = (uint8_t)op;
+        const bool stack_op = op >= MK_OP_PUSH && op <= MK_OP_IFF_S;
+        offs[i] = (uint16_t)(stack_op ? arg * (U * N * BLOCK) : arg * RowShape<N>::RS);
+    }
+    ops[p.n_instr] = (uint8_t)MK_OP_END;
+    offs[p.n_instr] = 0;
+}
+
 template <int N>
-__device__ __forceinline__ void load_atom(const uint32_t *row, int i, uint32_t (&x)[N]) {
+__device__ __forceinline__ void load_atom(const uint32_t *src, uint32_t (&x)[N]) {
     constexpr int RS = RowShape<N>::RS;
-    const uint4 *p = reinterpret_cast<const uint4 *>(row + i * RS);
+    const uint4 *p = reinterpret_cast<const uint4 *>(src);
     uint32_t t[RS];
 #pragma unroll
     for (int q = 0; q < RS / 4; ++q) {
@@ -173,22 +193,22 @@ __device__ __forceinline__ void dia_op(uint32_t (&a)[N], const uint32_t (&E)[N *
     }
 }
 
-// Run a validated program on U units.  rows[u]: the unit's atom row;
-// E[NE == 1 ? 0 : u]: the unit's frame word.  code must be readable one
-// byte past n_instr.
-template <int N, int U, int NE, int BLOCK>
-__device__ __forceinline__ void run_program(const uint8_t *code, int n_instr, const uint32_t *const (&rows)[U],
+// Run a decoded program on U units.  Unit u's atom row is row0 + u*ROWSTEP
+// (ROWSTEP = 0: all units share one valuation); its frame word is
+// E[NE == 1 ? 0 : u]; stack: this thread's column.
+template <int N, int U, int NE, int BLOCK, int ROWSTEP>
+__device__ __forceinline__ void run_program(const uint8_t *ops, const uint16_t *offs, const uint32_t *row0,
                                             const uint32_t (&E)[NE][N * N], uint32_t *stack,
                                             uint32_t (&A)[U][N]) {
-    uint32_t ins = code[0];
-    for (int pc = 0; pc < n_instr; ++pc) {
-        const uint32_t next = code[pc + 1];
-        const int arg = (int)(ins >> 4);
-        uint32_t *st = stack + arg * (U * N * BLOCK);
-        switch (ins & 15u) {
+    uint32_t op = ops[0], off = offs[0];
+    for (int pc = 1;; ++pc) {
+        const uint32_t op_next = ops[pc], off_next = offs[pc];
+        uint32_t *st = stack + off;
+        const uint32_t *rw = row0 + off;
+        switch (op) {
         case MK_OP_LDV:
 #pragma unroll
-            for (int u = 0; u < U; ++u) load_atom<N>(rows[u], arg, A[u]);
+            for (int u = 0; u < U; ++u) load_atom<N>(rw + u * ROWSTEP, A[u]);
             break;
         case MK_OP_LDT:
 #pragma unroll
@@ -256,7 +276,7 @@ __device__ __forceinline__ void run_program(const uint8_t *code, int n_instr, co
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 uint32_t x[N];
-                load_atom<N>(rows[u], arg, x);
+                load_atom<N>(rw + u * ROWSTEP, x);
 #pragma unroll
                 for (int w = 0; w < N; ++w) A[u][w] &= x[w];
             }
@@ -265,7 +285,7 @@ __device__ __forceinline__ void run_program(const uint8_t *code, int n_instr, co
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 uint32_t x[N];
-                load_atom<N>(rows[u], arg, x);
+                load_atom<N>(rw + u * ROWSTEP, x);
 #pragma unroll
                 for (int w = 0; w < N; ++w) A[u][w] |= x[w];
             }
@@ -274,22 +294,27 @@ __device__ __forceinline__ void run_program(const uint8_t *code, int n_instr, co
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 uint32_t x[N];
-                load_atom<N>(rows[u], arg, x);
+                load_atom<N>(rw + u * ROWSTEP, x);
 #pragma unroll
                 for (int w = 0; w < N; ++w) A[u][w] = ~A[u][w] | x[w];
             }
             break;
-        default:   // MK_OP_RIMP_V
+        case MK_OP_RIMP_V:
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 uint32_t x[N];
-                load_atom<N>(rows[u], arg, x);
+                load_atom<N>(rw + u * ROWSTEP, x);
 #pragma unroll
                 for (int w = 0; w < N; ++w) A[u][w] = ~x[w] | A[u][w];
             }
             break;
+        case MK_OP_END:
+            return;
+        default:
+            __builtin_unreachable();
         }
-        ins = next;
+        op = op_next;
+        off = off_next;
     }
 }
 
@@ -304,7 +329,7 @@ __device__ __forceinline__ bool program_ok(const mk_program &p) {
         if (op == MK_OP_LDV || op >= MK_OP_AND_V) {
             if (arg >= p.nvars) return false;
         } else if (op >= MK_OP_PUSH) {
-            if (arg >= MK_MAX_STACK) return false;
+            if (arg >= p.depth) return false;
         } else if (arg != 0) {
             return false;
         }

@@ -26,6 +26,7 @@
 namespace mkd {
 
 constexpr int SEP_ROW_CAP = 128;
+constexpr int SEP_OPS_STRIDE = MK_MAX_CODE + 2;
 
 struct SepArgs {
     const mk_program *phi;
@@ -46,7 +47,7 @@ struct SepArgs {
 
 template <int N, int U, int BLOCK>
 struct SepSmem {
-    static constexpr size_t code_bytes(int tile) { return ((size_t)tile * MK_MAX_CODE * 2 + 16 + 15) & ~(size_t)15; }
+    static constexpr size_t code_bytes(int tile) { return ((size_t)tile * SEP_OPS_STRIDE * 6 + 15) & ~(size_t)15; }
     static constexpr size_t meta_bytes(int tile) { return (size_t)tile * 24; }   // 4 int + u64
     static constexpr size_t row_bytes() { return (size_t)SEP_ROW_CAP * RowShape<N>::WORDS * 4; }
     static constexpr size_t stack_bytes() { return (size_t)MK_MAX_STACK * U * N * BLOCK * 4; }
@@ -85,8 +86,10 @@ __global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int s_active;
     const int tile = a.tile;
-    uint8_t *s_phi = smem;
-    uint8_t *s_psi = smem + (size_t)tile * MK_MAX_CODE;
+    uint16_t *s_offs_a = (uint16_t *)smem;
+    uint16_t *s_offs_b = s_offs_a + (size_t)tile * SEP_OPS_STRIDE;
+    uint8_t *s_ops_a = (uint8_t *)(s_offs_b + (size_t)tile * SEP_OPS_STRIDE);
+    uint8_t *s_ops_b = s_ops_a + (size_t)tile * SEP_OPS_STRIDE;
     int *s_na = (int *)(smem + SM::code_bytes(tile));
     int *s_nb = s_na + tile;
     int *s_k = s_nb + tile;
@@ -119,17 +122,14 @@ __global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
         s_nb[i] = pb.n_instr;
         s_k[i] = k;
         s_key[i] = ~0ull;
-        if (ok) atomicAdd(&s_active, 1);
+        if (ok) {
+            atomicAdd(&s_active, 1);
+            decode_program<N, U, BLOCK>(pa, s_ops_a + i * SEP_OPS_STRIDE, s_offs_a + i * SEP_OPS_STRIDE);
+            decode_program<N, U, BLOCK>(pb, s_ops_b + i * SEP_OPS_STRIDE, s_offs_b + i * SEP_OPS_STRIDE);
+        }
     }
     __syncthreads();
     if (s_active == 0) return;
-    for (int i = threadIdx.x; i < np * MK_MAX_CODE / 4; i += BLOCK) {
-        const int pi = i / (MK_MAX_CODE / 4), wi = i % (MK_MAX_CODE / 4);
-        ((uint32_t *)s_phi)[i] = ((const uint32_t *)a.phi[p0 + pi].code)[wi];
-        ((uint32_t *)s_psi)[i] = ((const uint32_t *)a.psi[p0 + pi].code)[wi];
-    }
-    if (threadIdx.x < 4) ((uint32_t *)(s_psi + (size_t)np * MK_MAX_CODE))[threadIdx.x] = 0;
-    // the bytes after phi's last program are psi's first: readable
 
     uint32_t E[U][N * N];
     uint32_t valid[U];
@@ -170,7 +170,8 @@ __global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
         const int k = s_k[fi];
         const bool exh = exhaustive_vals(k, N, a.S);
         const uint32_t nval = exh ? (1u << (k * N)) : a.S;
-        const uint8_t *ca = s_phi + fi * MK_MAX_CODE, *cb = s_psi + fi * MK_MAX_CODE;
+        const uint8_t *oa = s_ops_a + fi * SEP_OPS_STRIDE, *ob = s_ops_b + fi * SEP_OPS_STRIDE;
+        const uint16_t *fa = s_offs_a + fi * SEP_OPS_STRIDE, *fb = s_offs_b + fi * SEP_OPS_STRIDE;
         int best_o = U * 32, best_w = 0;     // o = u * 32 + lane: ascending frames
         uint32_t best_j = 0;
         for (uint32_t c0 = 0; c0 < nval; c0 += SEP_ROW_CAP) {
@@ -188,12 +189,9 @@ __global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
                 rows_c0 = c0;
             }
             for (uint32_t jj = 0; jj < cn && best_o > 0; ++jj) {
-                const uint32_t *rows[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) rows[u] = s_rows + jj * RW;
                 uint32_t A[U][N], B[U][N];
-                run_program<N, U, U, BLOCK>(ca, na, rows, E, s_stack, A);
-                run_program<N, U, U, BLOCK>(cb, nb, rows, E, s_stack, B);
+                run_program<N, U, U, BLOCK, 0>(oa, fa, s_rows + jj * RW, E, s_stack, A);
+                run_program<N, U, U, BLOCK, 0>(ob, fb, s_rows + jj * RW, E, s_stack, B);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     uint32_t any = 0;

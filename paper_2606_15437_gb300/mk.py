@@ -37,7 +37,7 @@ class mk_program(ctypes.Structure):
 
 
 class mk_tune(ctypes.Structure):
-    _fields_ = [("block", ctypes.c_uint16), ("tile", ctypes.c_uint16), ("words", ctypes.c_uint16),
+    _fields_ = [("block", ctypes.c_uint16), ("tile", ctypes.c_uint16), ("units", ctypes.c_uint16),
                 ("persistent", ctypes.c_uint16)]
 
 

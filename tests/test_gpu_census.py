@@ -66,13 +66,13 @@ def test_pr1_config_full():
     check_against_oracle(job, res, texts, (1, 2, 3))
 
 
-@pytest.mark.parametrize("tile,block", [(1, 128), (7, 256), (16, 256), (64, 128)])
-def test_random_formulas_sampled_valuations(tile, block):
+@pytest.mark.parametrize("tile,block,units", [(1, 128, 2), (7, 256, 4), (16, 256, 8), (64, 128, 4)])
+def test_random_formulas_sampled_valuations(tile, block, units):
     rng = random.Random(tile)
     texts = [W.random_formula(rng, rng.randint(1, 20), rng.randint(0, 4), rng.randint(0, 4))
              for _ in range(37)]
     job = engine().CensusJob(texts, CLS, 1, 4, samples=16, seed=tile,
-                             tune={"tile": tile, "block": block})
+                             tune={"tile": tile, "block": block, "units": units})
     res = job.run()
     check_against_oracle(job, res, texts, (1, 2, 3))
     # n = 4 on a subset (the oracle pays 2^16 frames each)
