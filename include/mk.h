@@ -169,6 +169,26 @@ int mk_census(const mk_program *d_progs, int32_t nprog, const mk_census_cfg *cfg
               mk_result *d_out, int32_t *d_status, void *d_workspace, size_t ws_bytes,
               void *stream);
 
+/* The census without a caller-provided workspace, for callers that cannot
+   allocate device memory: a C program or language binding that only passes
+   pointers it already owns, or code that must not call cudaMalloc/cudaFree
+   because they synchronise the device.  The paper has no counterpart; it
+   is a packaging of mk_census.  Arguments and results are those of
+   mk_census; the scratch space is a fixed array of MK_NOALLOC_SCRATCH_BYTES
+   inside the library, held on every GPU that loads it until the process
+   exits.  Configurations whose mk_census_workspace_size exceeds that limit
+   (S4 or S5 at n = 6) are rejected with MK_E_WORKSPACE before anything is
+   launched.  The first call on a device looks up the array's address
+   (cudaGetSymbolAddress) with that device current; make that first call
+   before any stream capture.  All calls share the one array, and it keeps
+   the last call's contents: every part of it that a call reads is written
+   by that call first, but calls whose work overlaps on the GPU (different
+   streams, or different host threads) race on it, so serialise them.
+   Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
+#define MK_NOALLOC_SCRATCH_BYTES (1u << 20)
+int mk_census_noalloc(const mk_program *d_progs, int32_t nprog, const mk_census_cfg *cfg,
+                      mk_result *d_out, int32_t *d_status, void *stream);
+
 /* Number of class-c frames on n worlds that mk_census enumerates (K: 2^(n^2),
    T: 2^(n^2-n), S4: preorders, S5: equivalence relations); 0 if n > 6. */
 uint64_t mk_class_frames(uint32_t cls, int32_t n);

@@ -96,6 +96,8 @@ _SIGS = {
     "mk_split_cert": (ctypes.c_int, [ctypes.POINTER(mk_program), ctypes.POINTER(mk_program), ctypes.c_char_p,
                                      ctypes.c_char_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
                                      ctypes.c_uint64, ctypes.POINTER(mk_cert)]),
+    "mk_census_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(mk_census_cfg),
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "mk_census_launches": (ctypes.c_int32, [ctypes.POINTER(mk_census_cfg), ctypes.c_int32]),
     "mk_calibrate_lop3": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32,
                                          ctypes.c_uint32, ctypes.c_void_p]),
@@ -202,6 +204,13 @@ def census_raw(d_progs, nprog, cfg, d_out, d_status, d_ws, ws_bytes, stream):
     """mk_census on raw device pointers (ints) and a cudaStream_t (int)."""
     _check(lib().mk_census(d_progs, nprog, ctypes.byref(cfg), d_out, d_status, d_ws, ws_bytes, stream),
            "mk_census")
+
+
+def census_noalloc_raw(d_progs, nprog, cfg, d_out, d_status, stream):
+    """mk_census_noalloc: the census with the library's own fixed scratch
+    array instead of a caller workspace (for callers that cannot allocate
+    device memory).  Returns the library's code (0 = ok)."""
+    return int(lib().mk_census_noalloc(d_progs, nprog, ctypes.byref(cfg), d_out, d_status, stream))
 
 
 def census_launches(cfg, nprog):
