@@ -45,7 +45,7 @@ extern "C" {
 #define MK_MAX_NODES 64          /* |phi| of a compiled formula               */
 #define MK_MAX_CODE 96           /* instructions per program (<= nodes + pushes) */
 #define MK_MAX_STACK 4           /* saved truth sets per program               */
-#define MK_MAX_VARS 4            /* p0..p3 (paper's limit, Sec. 12)            */
+#define MK_MAX_VARS 4            /* p0..p3 (paper's limit, Sec. 11)            */
 #define MK_MAX_WORLDS_EXH 6      /* exhaustive frames: K index < 2^36          */
 #define MK_MAX_WORLDS_SAMPLED 8  /* sampled separation frames                  */
 #define MK_MAX_CERT_WORLDS 32    /* certificates (u32 successor masks)         */
@@ -118,7 +118,7 @@ typedef struct {
 int mk_compile(const char *text, mk_program *out, int32_t *err_pos);
 
 /* Compile "phi <-> psi" into one program whose truth set is the set of
-   worlds where phi and psi agree (the biconditional of Prop. 6). */
+   worlds where phi and psi agree (the biconditional of Prop. 4). */
 int mk_compile_iff(const char *phi, const char *psi, mk_program *out, int32_t *err_pos);
 
 /* ----------------------------------------------------------- the census */
@@ -158,7 +158,7 @@ typedef struct {
 /* Workspace bytes mk_census needs for this configuration and batch. */
 size_t mk_census_workspace_size(const mk_census_cfg *cfg, int32_t nprog);
 
-/* Census (Alg. 1 over every selected (class, n) layer, Thm. 4): for each
+/* Census (Alg. 1 over every selected (class, n) layer, Thm. 2): for each
    program p, each selected class c (in the order K, T, S4, S5) and each
    n in [n_min, n_max], writes
        d_out[(p * ncls + c) * (n_max - n_min + 1) + (n - n_min)]
@@ -189,6 +189,68 @@ int mk_census(const mk_program *d_progs, int32_t nprog, const mk_census_cfg *cfg
 int mk_census_noalloc(const mk_program *d_progs, int32_t nprog, const mk_census_cfg *cfg,
                       mk_result *d_out, int32_t *d_status, void *stream);
 
+/* ------------------------------------------------------ uneven batches */
+/* Formulas of very different lengths, each with its own class and n_max,
+   evaluated in ONE persistent launch that takes work items from a queue
+   (Sec. 8 measures fused vs separate launches; here the fusion spans
+   classes, sizes and lengths).  The host builds a plan (mk_plan_uneven):
+   for every layer (class c, n) the jobs with that class and n_max >= n are
+   sorted by cost, cut into tiles of formulas of similar length, and every
+   tile is split into items of a few thousand frame words; items are
+   ordered longest first.  The caller copies the plan to device memory as
+   is; mk_census_uneven then clears the outputs, builds the S4/S5 lists,
+   resets the queue cursor and runs the persistent kernel -- all stream
+   operations, so the whole call can be captured in a CUDA graph (after one
+   uncaptured call, which sets kernel attributes). */
+typedef struct {
+    int32_t prog;          /* index into the program array                  */
+    uint8_t cls;           /* 0 K, 1 T, 2 S4, 3 S5                           */
+    uint8_t n_max;         /* layers n = 1..n_max, n_max <= 6                */
+    uint16_t reserved;
+} mk_job;
+
+typedef struct {
+    uint32_t lbeg;         /* first entry of the tile in the plan's job list */
+    uint16_t np;           /* jobs in the tile                               */
+    uint8_t n;             /* worlds                                         */
+    uint8_t cls;           /* 0 K, 1 T, 2 S4, 3 S5                           */
+    uint64_t w0, w1;       /* frame words [w0, w1) of the layer (32 frames   */
+                           /* per word, in class order)                      */
+} mk_work_item;            /* 24 bytes                                       */
+
+typedef struct {
+    uint64_t bytes;        /* plan size                                      */
+    uint32_t nitems;       /* work items                                     */
+    uint32_t nlist;        /* entries of the job list (one per job and n)    */
+    uint32_t list_off;     /* byte offset of the job list (uint32 job ids)   */
+    uint32_t items_off;    /* byte offset of the items (mk_work_item)        */
+    uint8_t n_max;         /* largest n over the jobs                        */
+    uint8_t max_depth;     /* largest program depth                          */
+    uint16_t block;        /* threads per CTA the plan was cut for           */
+    uint16_t units;        /* valuations per dispatched instruction          */
+    uint16_t tile_cap;     /* largest tile (formulas per work item)          */
+    double ops;            /* estimated logic ops of the batch               */
+} mk_plan_info;
+
+/* Build a plan (host).  tiles[4]: formulas per tile for programs of <= 8,
+   <= 16, <= 32 and more instructions (NULL: 16 each); tune: block and
+   units (zeros: 256 and 8).  h_plan == NULL only fills *info (size).
+   Returns MK_E_WORKSPACE if plan_bytes < info->bytes. */
+int mk_plan_uneven(const mk_program *h_progs, int32_t nprog, const mk_job *h_jobs, int32_t njobs,
+                   uint32_t samples, const uint16_t *tiles, const mk_tune *tune, void *h_plan,
+                   size_t plan_bytes, mk_plan_info *info);
+
+size_t mk_uneven_workspace_size(const mk_plan_info *info);
+
+/* Run the plan: for every job j and n <= its n_max, writes
+   d_out[j * 6 + (n - 1)] (results of the job's class on n worlds); entries
+   for n > n_max are left cleared (cm_count 0, no witness).  d_plan: the
+   plan bytes in device memory; d_samples: [(n_max+1) * S] as in the census. */
+int mk_census_uneven(const mk_program *d_progs, const mk_job *d_jobs, int32_t njobs, const void *d_plan,
+                     const mk_plan_info *info, uint32_t samples, const uint32_t *d_samples,
+                     mk_result *d_out, int32_t *d_status, void *d_workspace, size_t ws_bytes,
+                     void *stream);
+
 /* Number of class-c frames on n worlds that mk_census enumerates (K: 2^(n^2),
    T: 2^(n^2-n), S4: preorders, S5: equivalence relations); 0 if n > 6. */
 uint64_t mk_class_frames(uint32_t cls, int32_t n);
@@ -206,7 +268,7 @@ typedef struct {
     uint32_t val[MK_MAX_VARS];          /* variable masks                        */
 } mk_cert;
 
-/* Certificate check (Def. 1, Prop. 3), host only: its own parser and a
+/* Certificate check (Def. 1, Prop. 2), host only: its own parser and a
    recursive evaluator over explicit successor sets, sharing no code with the
    compiler or the kernels.  Returns 1 if valid (frame in class, and phi false
    at world -- or phi and psi differ there), 0 if not, < 0 if malformed. */
@@ -231,7 +293,7 @@ typedef struct {
     mk_tune tune;
 } mk_separate_cfg;
 
-/* Distinguishing-pair search (Def. 2, Prop. 6): for each pair i, the least
+/* Distinguishing-pair search (Def. 2, Prop. 4): for each pair i, the least
    (n, frame, valuation, world) at which phi_i and psi_i take different
    truth values, over the K frames of n_exh_min..n_exh_max worlds in K-index
    order, then the sampled relations of n_smp_min..n_smp_max worlds in sample
@@ -262,7 +324,7 @@ int mk_split_cert(const mk_program *h_phi, const mk_program *h_psi, const char *
 int32_t mk_census_launches(const mk_census_cfg *cfg, int32_t nprog);
 
 /* ------------------------------------------------------ calibration */
-/* Logic-op issue ceiling (the roofline denominator of the census; Sec. 10
+/* Logic-op issue ceiling (the roofline denominator of the census; Sec. 8
    measures the same uint32 logic ceiling): launches blocks x threads
    threads, each running independent chains of three-input logic ops for
    `iters` iterations; d_sink is a device word array of `blocks` entries. */

@@ -12,7 +12,7 @@
  *   formulas      phi ::= T | F | p_i | ~phi | phi&phi | phi|phi | phi->phi
  *                         | []phi | <>phi                     (Sec. 2)
  *                 (phi<->psi is accepted as sugar for the biconditional of
- *                  Prop. 6.)
+ *                  Prop. 4.)
  *   satisfaction  w |= []phi iff for all v, R(w,v) implies v |= phi;
  *                 w |= <>phi iff some v has R(w,v) and v |= phi   (Sec. 2)
  *   classes       K all frames, T reflexive, S4 reflexive+transitive,
@@ -23,7 +23,7 @@
  *                 and the lexicographically least (frame, valuation, world)
  *                 witness -- the outputs of the corpus scan of Alg. 1 (Sec. 4)
  *   separation    the least (n, frame, valuation, world) at which phi and
- *                 psi take different truth values (Def. 2, Prop. 6, Sec. 7)
+ *                 psi take different truth values (Def. 2, Prop. 4, Sec. 7)
  *
  * Readings of the paper where it is silent (each is listed in the design doc):
  *   - frame index f of an n-world frame: R(w,v) is bit (w*n+v) of f

@@ -1,4 +1,4 @@
-// mk_calib.cu -- integer logic-op issue-rate calibration (Sec. 10's uint32
+// mk_calib.cu -- integer logic-op issue-rate calibration (Sec. 8's uint32
 // XOR/AND/OR ceiling, measured here as three-input LOP3 throughput).
 //
 // Each thread runs MK_CALIB_CHAINS independent dependency chains of

@@ -1,8 +1,8 @@
 // mk_certify.cpp -- independent certificate checker (host).
 //
-// Def. 1 / Prop. 3 (Sec. 5): a certificate (phi, n, succ, V, w, C) is valid
+// Def. 1 / Prop. 2 (Sec. 5): a certificate (phi, n, succ, V, w, C) is valid
 // iff the frame belongs to class C and M,w does not satisfy phi.  For a
-// separation certificate (Prop. 6) the pointed model must give phi and psi
+// separation certificate (Prop. 4) the pointed model must give phi and psi
 // different truth values.  The checker is the trust anchor of the search, so
 // it shares nothing with the compiler or the kernels: it has its own
 // tokenizer and parser, keeps a frame as explicit successor lists, and

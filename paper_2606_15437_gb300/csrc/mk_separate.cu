@@ -1,7 +1,7 @@
-// mk_separate.cu -- distinguishing-pair search (Def. 2, Prop. 6).
+// mk_separate.cu -- distinguishing-pair search (Def. 2, Prop. 4).
 //
 // A pair (phi, psi) is separated on a pointed model iff their truth sets
-// differ there, i.e. iff the biconditional phi <-> psi is refuted (Prop. 6).
+// differ there, i.e. iff the biconditional phi <-> psi is refuted (Prop. 4).
 // The kernel runs both programs on the same bit-sliced frame words (U words
 // per thread, one valuation at a time), takes d[w] = t_phi[w] ^ t_psi[w]
 // per world and keeps the least (frame, valuation, world) with a set bit,
@@ -48,7 +48,9 @@ struct SepArgs {
 template <int N, int U, int BLOCK>
 struct SepSmem {
     static constexpr size_t code_bytes(int tile) { return ((size_t)tile * SEP_OPS_STRIDE * 6 + 15) & ~(size_t)15; }
-    static constexpr size_t meta_bytes(int tile) { return (size_t)tile * 24; }   // 4 int + u64
+    // 4 int + u64 per pair, rounded up so the atom rows after it stay
+    // 16-byte aligned (they are read with 16-byte loads)
+    static constexpr size_t meta_bytes(int tile) { return ((size_t)tile * 24 + 15) & ~(size_t)15; }
     static constexpr size_t row_bytes() { return (size_t)SEP_ROW_CAP * RowShape<N>::WORDS * 4; }
     static constexpr size_t stack_bytes() { return (size_t)MK_MAX_STACK * U * N * BLOCK * 4; }
     static size_t total(int tile) { return code_bytes(tile) + meta_bytes(tile) + row_bytes() + stack_bytes(); }

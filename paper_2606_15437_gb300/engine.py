@@ -162,3 +162,78 @@ class SeparateJob:
         a, b = self.pairs[i]
         return mk.split_cert(mk.program_at(self.pa, i), mk.program_at(self.pb, i), a, b, self.seed,
                              self.S, samples_n, int(key))
+
+
+class UnevenJob:
+    """An uneven batch: every formula has its own class and n_max, all of
+    them evaluated by one persistent launch over a host-built work plan
+    (mk_plan_uneven / mk_census_uneven).  ``capture()`` records the whole
+    call (clear, lists, queue reset, persistent kernel) as one CUDA graph."""
+
+    def __init__(self, items, samples=64, seed=3, tiles=None, tune=None, device="cuda"):
+        if not torch.cuda.is_available():
+            raise RuntimeError("UnevenJob needs a CUDA device (there is no CPU fallback)")
+        self.items = list(items)                       # (text, class name, n_max)
+        self.texts = [t for t, _, _ in self.items]
+        self.progs = mk.compile_batch(self.texts)
+        self.njobs = len(self.items)
+        self.jobs = np.zeros(self.njobs, mk.JOB_DTYPE)
+        self.jobs["prog"] = np.arange(self.njobs)
+        self.jobs["cls"] = [CLASSES.index(c) for _, c, _ in self.items]
+        self.jobs["n_max"] = [n for _, _, n in self.items]
+        self.S = samples
+        self.seed = seed
+        self.device = torch.device(device)
+        self.plan, self.info = mk.plan_uneven(self.progs, self.jobs, samples, tiles, tune)
+        n_max = int(self.info.n_max)
+        self.sample_table = workloads.valuation_table(seed, samples, n_max) if samples else None
+        self.d_progs = _dev_bytes(self.progs, self.device)
+        self.d_jobs = _dev_bytes(self.jobs, self.device)
+        self.d_plan = _dev_bytes(self.plan, self.device)
+        self.d_samples = _dev_bytes(self.sample_table, self.device) if samples else None
+        self.ws_bytes = mk.uneven_workspace_size(self.info)
+        self.d_ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        self.d_out = torch.empty(self.njobs * 6 * 3, dtype=torch.int64, device=self.device)
+        self.d_status = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.graph = None
+
+    def launch(self, stream=None):
+        mk.census_uneven_raw(self.d_progs.data_ptr(), self.d_jobs.data_ptr(), self.njobs,
+                             self.d_plan.data_ptr(), self.info, self.S,
+                             self.d_samples.data_ptr() if self.S else None, self.d_out.data_ptr(),
+                             self.d_status.data_ptr(), self.d_ws.data_ptr(), self.ws_bytes, _stream_ptr(stream))
+
+    def capture(self):
+        """Record one launch as a CUDA graph (after an uncaptured warm-up)."""
+        self.launch()
+        torch.cuda.synchronize(self.device)
+        self.graph = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(self.device)
+        with torch.cuda.graph(self.graph, stream=s):
+            self.launch(s)
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
+
+    def results(self):
+        """uint64[njobs, 6, 3]: (cm_count, frames_refuted, witness_key) for n = 1..6."""
+        torch.cuda.synchronize(self.device)
+        st = int(self.d_status.item())
+        if st:
+            raise mk.MkError(mk.status_error(st), "device status 0x%x" % st)
+        return self.d_out.cpu().numpy().view(np.uint64).reshape(self.njobs, 6, 3)
+
+    def evals(self):
+        total = 0
+        for (t, c, nmax), p in zip(self.items, self.progs):
+            for n in range(1, nmax + 1):
+                total += mk.class_frames(c, n) * n_valuations(int(p["nvars"]), n, self.S)
+        return total
+
+    def buckets(self):
+        """Jobs grouped by (class, n_max): the per-bucket plain-launch baseline."""
+        groups = {}
+        for j, (t, c, nmax) in enumerate(self.items):
+            groups.setdefault((c, nmax), []).append(j)
+        return groups

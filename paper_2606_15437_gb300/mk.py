@@ -59,6 +59,21 @@ class mk_cert(ctypes.Structure):
                 ("succ", ctypes.c_uint32 * MK_MAX_CERT_WORLDS), ("val", ctypes.c_uint32 * MK_MAX_VARS)]
 
 
+class mk_job(ctypes.Structure):
+    _fields_ = [("prog", ctypes.c_int32), ("cls", ctypes.c_uint8), ("n_max", ctypes.c_uint8),
+                ("reserved", ctypes.c_uint16)]
+
+
+class mk_plan_info(ctypes.Structure):
+    _fields_ = [("bytes", ctypes.c_uint64), ("nitems", ctypes.c_uint32), ("nlist", ctypes.c_uint32),
+                ("list_off", ctypes.c_uint32), ("items_off", ctypes.c_uint32), ("n_max", ctypes.c_uint8),
+                ("max_depth", ctypes.c_uint8), ("block", ctypes.c_uint16), ("units", ctypes.c_uint16),
+                ("tile_cap", ctypes.c_uint16), ("ops", ctypes.c_double)]
+
+
+JOB_DTYPE = np.dtype([("prog", "<i4"), ("cls", "u1"), ("n_max", "u1"), ("reserved", "<u2")])
+
+
 class mk_separate_cfg(ctypes.Structure):
     _fields_ = [("n_exh_min", ctypes.c_uint8), ("n_exh_max", ctypes.c_uint8),
                 ("n_smp_min", ctypes.c_uint8), ("n_smp_max", ctypes.c_uint8),
@@ -102,6 +117,14 @@ _SIGS = {
     "mk_calibrate_lop3": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32,
                                          ctypes.c_uint32, ctypes.c_void_p]),
     "mk_calibrate_ops_per_launch": (ctypes.c_uint64, [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32]),
+    "mk_plan_uneven": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                      ctypes.c_uint32, ctypes.c_void_p, ctypes.POINTER(mk_tune), ctypes.c_void_p,
+                                      ctypes.c_size_t, ctypes.POINTER(mk_plan_info)]),
+    "mk_uneven_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(mk_plan_info)]),
+    "mk_census_uneven": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                        ctypes.POINTER(mk_plan_info), ctypes.c_uint32, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                        ctypes.c_void_p]),
     "mk_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mk_status_error": (ctypes.c_int, [ctypes.c_int32]),
     "mk_version": (ctypes.c_int, []),
@@ -322,3 +345,35 @@ def separate_raw(d_phi, d_psi, npairs, cfg, d_split, d_status, d_ws, ws_bytes, s
 
 def separate_workspace_size(cfg, npairs):
     return int(lib().mk_separate_workspace_size(ctypes.byref(cfg), npairs))
+
+
+# ------------------------------------------------------ uneven batches
+
+def plan_uneven(progs, jobs, samples, tiles=None, tune=None):
+    """mk_plan_uneven: returns (plan bytes as a numpy uint8 array, mk_plan_info)."""
+    progs = np.ascontiguousarray(progs)
+    jobs = np.ascontiguousarray(jobs)
+    info = mk_plan_info()
+    t = mk_tune()
+    if tune:
+        for k, v in tune.items():
+            setattr(t, k, v)
+    tl = None if tiles is None else np.ascontiguousarray(np.asarray(tiles, np.uint16))
+    tl_ptr = None if tl is None else tl.ctypes.data_as(ctypes.c_void_p)
+    args = (progs.ctypes.data_as(ctypes.c_void_p), len(progs), jobs.ctypes.data_as(ctypes.c_void_p),
+            len(jobs), samples, tl_ptr, ctypes.byref(t))
+    _check(lib().mk_plan_uneven(*args, None, 0, ctypes.byref(info)), "mk_plan_uneven")
+    plan = np.zeros(int(info.bytes), np.uint8)
+    _check(lib().mk_plan_uneven(*args, plan.ctypes.data_as(ctypes.c_void_p), plan.nbytes, ctypes.byref(info)),
+           "mk_plan_uneven")
+    return plan, info
+
+
+def uneven_workspace_size(info):
+    return int(lib().mk_uneven_workspace_size(ctypes.byref(info)))
+
+
+def census_uneven_raw(d_progs, d_jobs, njobs, d_plan, info, samples, d_samples, d_out, d_status, d_ws,
+                      ws_bytes, stream):
+    _check(lib().mk_census_uneven(d_progs, d_jobs, njobs, d_plan, ctypes.byref(info), samples, d_samples,
+                                  d_out, d_status, d_ws, ws_bytes, stream), "mk_census_uneven")

@@ -57,7 +57,7 @@ def test_pairs_with_variables_sampled_valuations():
 
 
 def test_alpha_family_exhaustive_six_worlds():
-    # Prop. 7 / Table 3: alpha_1/alpha_2 split first at 4 worlds (K index
+    # Prop. 5 / Table 3: alpha_1/alpha_2 split first at 4 worlds (K index
     # 328, world 1), alpha_2/alpha_3 at 6 worlds (K index 17,335,328, world 2)
     pairs = [(W.alpha(1), W.alpha(2)), (W.alpha(2), W.alpha(3))]
     job = engine().SeparateJob(pairs, 1, 6)

@@ -157,7 +157,7 @@ def test_b_axiom_valid_exactly_on_symmetric(n):
     assert r["frames_refuted"] == 2 ** (n * n) - 2 ** (n * (n + 1) // 2)
 
 
-# ------------------------------------------- frame correspondence (Table 8)
+# ------------------------------------------- frame correspondence (Table 9)
 
 def _conds(n):
     def R(f, w, v):
@@ -180,13 +180,13 @@ def _conds(n):
     }
 
 
-TABLE8 = [("[]p -> p", "reflexive"), ("[]p -> <>p", "serial"), ("[]p -> [][]p", "transitive"),
+CORRESPONDENCES = [("[]p -> p", "reflexive"), ("[]p -> <>p", "serial"), ("[]p -> [][]p", "transitive"),
           ("<>p -> []<>p", "euclidean"), ("p -> []<>p", "symmetric"),
           ("<>p -> []p", "partial_function"), ("[][]p -> []p", "dense"),
           ("<>[]p -> []<>p", "confluent")]
 
 
-@pytest.mark.parametrize("axiom,cond", TABLE8)
+@pytest.mark.parametrize("axiom,cond", CORRESPONDENCES)
 @pytest.mark.parametrize("n", [1, 2, 3])
 def test_correspondence(axiom, cond, n):
     valid = oracle.frame_valid_all(axiom, n)
@@ -219,7 +219,7 @@ def test_alpha1_alpha2_first_split_at_four():
 
 @pytest.mark.slow
 def test_alpha2_alpha3_agree_through_five_split_at_six():
-    # Prop. 7: agreement on every frame of at most five worlds ...
+    # Prop. 5: agreement on every frame of at most five worlds ...
     for n in (1, 2, 3, 4, 5):
         assert oracle.pair_layer(alpha(2), alpha(3), n)["split"] is None
     # ... and a split at six worlds; the first one in K-index order:
@@ -233,7 +233,7 @@ def test_alpha2_alpha3_agree_through_five_split_at_six():
 
 
 def test_paper_certificate_alpha2_alpha3_path():
-    # Prop. 7: successor masks (2,4,8,16,32,0), falsifying world w0
+    # Prop. 5: successor masks (2,4,8,16,32,0), falsifying world w0
     succ = [2, 4, 8, 16, 32, 0]
     n = 6
     R = np.array([[(succ[w] >> v) & 1 for v in range(n)] for w in range(n)], np.uint8)
@@ -245,7 +245,7 @@ def test_paper_certificate_alpha2_alpha3_path():
 
 @pytest.mark.parametrize("m", [1, 2, 3, 4, 5])
 def test_lemma8_path_family(m):
-    # Lemma 8: on a directed path, alpha_m is false exactly at worlds with
+    # Lemma 2: on a directed path, alpha_m is false exactly at worlds with
     # r in {1, 3, ..., 2m-1} edges remaining to the dead end
     for L in (2 * m + 2, 2 * m + 5, 32):
         R = np.zeros((L, L), np.uint8)
