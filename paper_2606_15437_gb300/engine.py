@@ -237,3 +237,92 @@ class UnevenJob:
         for j, (t, c, nmax) in enumerate(self.items):
             groups.setdefault((c, nmax), []).append(j)
         return groups
+
+
+# ------------------------------------------------------------------ autotuner
+
+_TUNE_CACHE = None
+
+
+def _cache_path():
+    import os
+    return os.path.join(os.path.dirname(mk.LIB_PATH), "autotune.json")
+
+
+def _load_cache():
+    import json
+    import os
+    global _TUNE_CACHE
+    if _TUNE_CACHE is None:
+        p = _cache_path()
+        _TUNE_CACHE = json.load(open(p)) if os.path.exists(p) else {}
+    return _TUNE_CACHE
+
+
+def _store_cache():
+    import json
+    json.dump(_TUNE_CACHE, open(_cache_path(), "w"), indent=1, sort_keys=True)
+
+
+def _time_graph(job, reps=2):
+    job.launch()
+    job.results()
+    job.capture()
+    torch.cuda.synchronize(job.device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        job.replay()
+    e1.record()
+    torch.cuda.synchronize(job.device)
+    return e0.elapsed_time(e1) / reps
+
+
+def autotune_uneven(items, samples=64, seed=3, sample_size=2400, device="cuda", use_cache=True, log=None):
+    """Pick the persistent launch's CTA size, valuations per dispatched
+    instruction (units) and formulas per tile for each length bucket.
+
+    Coordinate descent on a stratified sample of the batch (every length
+    bucket and class represented in proportion): first (units, block) with
+    16-formula tiles, then each bucket's tile size in {4, 8, 16, 32, 64} with
+    the others fixed; each candidate is timed as a CUDA-graph replay.  The
+    choice is cached per (GPU name, SM count, samples, n_max set)."""
+    props = torch.cuda.get_device_properties(torch.device(device))
+    nmaxes = sorted({n for _, _, n in items})
+    key = "%s|%d|uneven|S=%d|n=%s" % (props.name, props.multi_processor_count, samples, nmaxes)
+    cache = _load_cache()
+    if use_cache and key in cache:
+        return cache[key]
+    step = max(1, len(items) // sample_size)
+    sample = items[::step]
+    trials = []
+
+    def run(units, block, tiles):
+        job = UnevenJob(sample, samples=samples, seed=seed, tiles=tiles, tune={"units": units, "block": block},
+                        device=device)
+        ms = _time_graph(job)
+        trials.append({"units": units, "block": block, "tiles": list(tiles), "ms": ms})
+        if log:
+            log("autotune units=%d block=%d tiles=%s: %.2f ms" % (units, block, tiles, ms))
+        return ms
+
+    best = None
+    for units in (4, 8):
+        for block in (128, 256):
+            ms = run(units, block, (16, 16, 16, 16))
+            if best is None or ms < best[0]:
+                best = (ms, units, block, [16, 16, 16, 16])
+    _, units, block, tiles = best
+    for b in range(4):
+        for t in (4, 8, 32, 64):
+            cand = list(tiles)
+            cand[b] = t
+            ms = run(units, block, tuple(cand))
+            if ms < best[0]:
+                best = (ms, units, block, cand)
+                tiles = cand
+    choice = {"units": best[1], "block": best[2], "tiles": best[3], "ms_sample": best[0],
+              "sample_size": len(sample), "trials": trials}
+    cache[key] = choice
+    _store_cache()
+    return choice
