@@ -299,7 +299,7 @@ typedef struct {
    order, then the sampled relations of n_smp_min..n_smp_max worlds in sample
    order (sizes are searched in that order; a pair with a split at one size is
    not searched at later sizes).  Writes d_split[i] = the packed key
-       n << 60 | f << 24 | x << 3 | w
+       sampled << 63 | (n - 1) << 60 | f << 24 | x << 3 | w
    (f: K index or sample number < 2^36; x < 2^21; w < 8), UINT64_MAX if the
    pair agrees everywhere searched.  Relations of sampled sizes come from
    mk_sample_relation(seed, n, s). */
@@ -332,6 +332,66 @@ int mk_calibrate_lop3(uint32_t *d_sink, int32_t blocks, int32_t threads, uint32_
                       uint32_t seed, void *stream);
 /* Logic ops one such launch performs. */
 uint64_t mk_calibrate_ops_per_launch(int32_t blocks, int32_t threads, uint32_t iters);
+
+/* ------------------------------------------------------ learned proposal */
+/* Truth vectors and the pair-ranking MLP.  Sec. 9 ranks candidate pairs by
+   small-frame semantic representations and verifies every hit exactly; here
+   the representation is a truth vector and the ranking a small MLP trained
+   on pairs the exact search has labelled.  The exact separation search
+   (mk_separate) and mk_certify remain the only judges of a hit. */
+typedef struct {
+    uint64_t frame;        /* K index of the model's frame                  */
+    uint32_t val;          /* valuation value (p_i at w: bit i*n+w)          */
+    uint8_t n;             /* worlds, 1..6                                   */
+    uint8_t world;         /* pointed world                                  */
+    uint16_t reserved;
+} mk_model;                /* 16 bytes                                       */
+
+/* Truth vectors: bit j of formula p's vector (word j/32 of row p, rows of
+   ngroups words) = program p is true at world models[j].world of model j.
+   Models come in groups of 32 with one n per group (h_group_n[g], host);
+   d_models holds 32*ngroups models. */
+int mk_fingerprint(const mk_program *d_progs, int32_t nprog, const mk_model *d_models,
+                   const int32_t *h_group_n, int32_t ngroups, uint32_t *d_bits, int32_t *d_status,
+                   void *stream);
+
+/* Exact k nearest neighbours of every vector in Hamming distance (self
+   excluded): d_nbr[q*k + i] / d_dist[q*k + i] list, for each query q, all
+   vectors with distance < t and the lowest-index ones with distance == t,
+   where t is the least distance reaching k neighbours; -1 / 0xFFFF pad
+   when fewer than k other vectors exist.  words: 32-bit words per vector. */
+size_t mk_knn_workspace_size(int32_t nvec);
+int mk_hamming_knn(const uint32_t *d_bits, int32_t nvec, int32_t words, int32_t k, int32_t *d_nbr,
+                   uint16_t *d_dist, void *d_workspace, size_t ws_bytes, void *stream);
+
+/* The MLP: x = [a xor b, a and b] for the truth vectors a, b of a pair
+   (features = 64 * words per vector), h1 = relu(x W1 + b1), h2 = relu(h1 W2
+   + b2), logit = h2 . w3 + b3.  Parameters are one FP32 buffer in the order
+   W1[features][hidden], b1, W2[hidden][hidden], b2, w3[hidden], b3.
+   Pairs are given by vector indices d_pa[i], d_pb[i]. */
+size_t mk_mlp_param_count(int32_t features, int32_t hidden);
+size_t mk_mlp_workspace_size(int32_t batch, int32_t hidden);
+int mk_mlp_forward(const float *d_params, int32_t features, int32_t hidden, const uint32_t *d_vec,
+                   const int32_t *d_pa, const int32_t *d_pb, int32_t batch, float *d_logits,
+                   void *d_workspace, size_t ws_bytes, void *stream);
+/* Gradient of the weighted binary cross-entropy sum_i w_i * BCE(logit_i, y_i)
+   (d_w may be NULL for weight 1) with respect to every parameter, in the
+   parameter layout, into d_grad; the loss into *d_loss.  FP32 throughout. */
+size_t mk_mlp_train_workspace_size(int32_t batch, int32_t features, int32_t hidden);
+int mk_mlp_gradient(const float *d_params, int32_t features, int32_t hidden, const uint32_t *d_vec,
+                    const int32_t *d_pa, const int32_t *d_pb, const float *d_y, const float *d_w,
+                    int32_t batch, float *d_grad, float *d_loss, void *d_workspace, size_t ws_bytes,
+                    void *stream);
+/* One Adam step (Kingma and Ba, 2015) on n parameters; step counts from 1. */
+int mk_adam_step(float *d_params, const float *d_grad, float *d_m, float *d_v, size_t n, float lr,
+                 float beta1, float beta2, float eps, int32_t step, float grad_scale, void *stream);
+/* Scoring with the first layer on the tensor cores in BF16 (the 0/1
+   features are exact; W1 is rounded to BF16), FP32 accumulation; hidden
+   must be 256. */
+size_t mk_mlp_infer_workspace_size(int32_t batch, int32_t features, int32_t hidden);
+int mk_mlp_infer_bf16(const float *d_params, int32_t features, int32_t hidden, const uint32_t *d_vec,
+                      const int32_t *d_pa, const int32_t *d_pb, int32_t batch, float *d_logits,
+                      void *d_workspace, size_t ws_bytes, void *stream);
 
 /* ------------------------------------------------------------- misc */
 const char *mk_strerror(int code);

@@ -337,6 +337,13 @@ __device__ __forceinline__ bool program_ok(const mk_program &p) {
     return true;
 }
 
+// Separation split key: sampled << 63 | (n-1) << 60 | f << 24 | x << 3 | w
+// (f < 2^36: K index or sample number; x < 2^21; w < 8).  Exhaustive sizes
+// are searched before sampled ones, so the key order is the search order.
+__host__ __device__ __forceinline__ uint64_t split_key(int sampled, int n, uint64_t f, uint64_t x, uint64_t w) {
+    return ((uint64_t)(sampled ? 1 : 0) << 63) | ((uint64_t)(n - 1) << 60) | (f << 24) | (x << 3) | w;
+}
+
 // Valuation set of a layer: exhaustive iff S == 0, k <= 1 or 2^(k n) <= S.
 __host__ __device__ __forceinline__ bool exhaustive_vals(int k, int n, uint32_t S) {
     if (S == 0 || k <= 1) return true;

@@ -101,8 +101,7 @@ __global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
     uint32_t *s_stack = (uint32_t *)((uint8_t *)s_rows + SM::row_bytes()) + threadIdx.x;
 
     const uint64_t cta_word0 = a.word_lo + (uint64_t)blockIdx.x * BLOCK * U;
-    const unsigned long long floor_key =
-        ((unsigned long long)N << 60) | ((unsigned long long)(cta_word0 << 5) << 24);
+    const unsigned long long floor_key = split_key(a.sampled, N, cta_word0 << 5, 0, 0);
     if (threadIdx.x == 0) s_active = 0;
     __syncthreads();
     const int p0 = blockIdx.y * tile;
@@ -223,7 +222,7 @@ __global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
             uint64_t my = 0;
             if (lane == src_lane) {
                 const uint64_t f = ((cta_word0 + (uint64_t)threadIdx.x * U) << 5) + (uint64_t)best_o;
-                my = ((uint64_t)N << 60) | (f << 24) | ((uint64_t)best_j << 3) | (uint64_t)best_w;
+                my = split_key(a.sampled, N, f, best_j, (uint64_t)best_w);
             }
             const uint64_t key = __shfl_sync(0xFFFFFFFFu, my, src_lane);
             if (lane == 0) atomicMin(&s_key[fi], (unsigned long long)key);
@@ -371,7 +370,8 @@ extern "C" int mk_split_cert(const mk_program *h_phi, const mk_program *h_psi, c
                              const char *psi, uint64_t seed, uint32_t samples, const uint32_t *h_samples_n,
                              uint64_t key, mk_cert *out) {
     if (!h_phi || !h_psi || !phi || !psi || !out || key == ~0ull) return MK_E_ARG;
-    const int n = (int)(key >> 60);
+    const int sampled = (int)(key >> 63);
+    const int n = (int)((key >> 60) & 7u) + 1;
     const uint64_t f = (key >> 24) & ((1ull << 36) - 1);
     const uint32_t j = (uint32_t)((key >> 3) & ((1u << 21) - 1));
     const int w = (int)(key & 7u);
@@ -379,7 +379,8 @@ extern "C" int mk_split_cert(const mk_program *h_phi, const mk_program *h_psi, c
     const int k = h_phi->nvars > h_psi->nvars ? h_phi->nvars : h_psi->nvars;
     const bool exh = exhaustive_vals(k, n, samples);
     if (!exh && !h_samples_n) return MK_E_ARG;
-    const uint64_t rel = n <= MK_MAX_WORLDS_EXH ? f : sample_relation(sm_stream(seed, 2, (uint64_t)n), n, f);
+    if (!sampled && n > MK_MAX_WORLDS_EXH) return MK_E_ARG;
+    const uint64_t rel = sampled ? sample_relation(sm_stream(seed, 2, (uint64_t)n), n, f) : f;
     const uint32_t x = exh ? j : h_samples_n[j];
     const uint32_t full = (1u << n) - 1u;
     std::memset(out, 0, sizeof(*out));

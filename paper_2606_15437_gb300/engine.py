@@ -157,7 +157,7 @@ class SeparateJob:
         return self.results()
 
     def certificate(self, i, key):
-        n = int(key) >> 60
+        n = mk.split_n(key)
         samples_n = self.sample_table[n] if self.S else None
         a, b = self.pairs[i]
         return mk.split_cert(mk.program_at(self.pa, i), mk.program_at(self.pb, i), a, b, self.seed,
@@ -326,3 +326,290 @@ def autotune_uneven(items, samples=64, seed=3, sample_size=2400, device="cuda", 
     cache[key] = choice
     _store_cache()
     return choice
+
+
+# ----------------------------------------------------------- learned proposal
+
+def truth_vectors(texts=None, progs=None, models=None, groups=None, seed=5, device="cuda"):
+    """uint32 device tensor [len(texts)][ngroups]: formula i's truth value at
+    each seeded pointed model (mk_fingerprint)."""
+    if progs is None:
+        progs = mk.compile_batch(texts)
+    if models is None:
+        models, groups = workloads.pointed_models(seed)
+    dev = torch.device(device)
+    d_progs = _dev_bytes(progs, dev)
+    d_models = _dev_bytes(models, dev)
+    bits = torch.zeros(len(progs) * len(groups), dtype=torch.int32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    mk.fingerprint_raw(d_progs.data_ptr(), len(progs), d_models.data_ptr(), groups, bits.data_ptr(),
+                       status.data_ptr(), _stream_ptr(None))
+    torch.cuda.synchronize(dev)
+    if int(status.item()):
+        raise mk.MkError(mk.status_error(int(status.item())), "mk_fingerprint")
+    return bits.view(len(progs), len(groups))
+
+
+def hamming_knn(bits, k):
+    """Exact k nearest neighbours of every truth vector (mk_hamming_knn):
+    (neighbour indices int32 [n][k], distances uint16 [n][k]) on the host."""
+    n, words = bits.shape
+    dev = bits.device
+    ws = torch.empty(mk.knn_workspace_size(n), dtype=torch.uint8, device=dev)
+    nbr = torch.empty(n * k, dtype=torch.int32, device=dev)
+    dist = torch.empty(n * k, dtype=torch.int16, device=dev)
+    mk.hamming_knn_raw(bits.data_ptr(), n, words, k, nbr.data_ptr(), dist.data_ptr(), ws.data_ptr(), ws.numel(),
+                       _stream_ptr(None))
+    torch.cuda.synchronize(dev)
+    return nbr.cpu().numpy().reshape(n, k), dist.cpu().numpy().view(np.uint16).reshape(n, k)
+
+
+def knn_universe(nbr, target, seed=0):
+    """Candidate pairs (i < j): the union of every formula's neighbour list,
+    cut or filled with seeded random pairs to ``target`` pairs."""
+    n, k = nbr.shape
+    i = np.repeat(np.arange(n, dtype=np.int64), k)
+    j = nbr.reshape(-1).astype(np.int64)
+    ok = j >= 0
+    a, b = np.minimum(i[ok], j[ok]), np.maximum(i[ok], j[ok])
+    code = np.unique(a * n + b)
+    rng = np.random.default_rng(seed)
+    if len(code) > target:
+        code = np.sort(rng.choice(code, target, replace=False))
+    while len(code) < target:
+        x = rng.integers(0, n, size=2 * (target - len(code)))
+        y = rng.integers(0, n, size=len(x))
+        keep = x != y
+        extra = np.minimum(x[keep], y[keep]) * n + np.maximum(x[keep], y[keep])
+        code = np.unique(np.concatenate([code, extra]))[:target] if len(code) + len(extra) >= target else \
+            np.unique(np.concatenate([code, extra]))
+    return (code // n).astype(np.int32), (code % n).astype(np.int32)
+
+
+class MLP:
+    """The pair-ranking network, trained and run by libmk's kernels
+    (mk_mlp_gradient + mk_adam_step for FP32 training, mk_mlp_infer_bf16 for
+    scoring).  Torch only holds the device buffers."""
+
+    def __init__(self, features, hidden=256, seed=0, device="cuda"):
+        self.F, self.H = features, hidden
+        self.dev = torch.device(device)
+        self.n = mk.mlp_param_count(features, hidden)
+        g = torch.Generator().manual_seed(seed)
+        F, H = features, hidden
+        parts = [torch.randn(F * H, generator=g) * (2.0 / F) ** 0.5, torch.zeros(H),
+                 torch.randn(H * H, generator=g) * (2.0 / H) ** 0.5, torch.zeros(H),
+                 torch.randn(H, generator=g) * (1.0 / H) ** 0.5, torch.zeros(1)]
+        self.params = torch.cat(parts).float().to(self.dev)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.grad = torch.zeros_like(self.params)
+        self.step = 0
+
+    def gradient(self, vec, pa, pb, y, w=None):
+        """Loss and gradient on one batch (device tensors)."""
+        B = len(pa)
+        ws = torch.empty(mk.mlp_train_workspace_size(B, self.F, self.H), dtype=torch.uint8, device=self.dev)
+        loss = torch.zeros(1, dtype=torch.float32, device=self.dev)
+        mk.mlp_gradient_raw(self.params.data_ptr(), self.F, self.H, vec.data_ptr(), pa.data_ptr(), pb.data_ptr(),
+                            y.data_ptr(), w.data_ptr() if w is not None else None, B, self.grad.data_ptr(),
+                            loss.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(None))
+        return loss
+
+    def train(self, vec, pa, pb, y, w=None, epochs=8, batch=4096, lr=1e-3, seed=0, log=None):
+        """Adam on the weighted binary cross-entropy, mean over each batch."""
+        n = len(pa)
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        history = []
+        for ep in range(epochs):
+            perm = torch.randperm(n, generator=g).to(self.dev)
+            tot = 0.0
+            for s in range(0, n, batch):
+                idx = perm[s:s + batch]
+                bpa, bpb, by = pa[idx].contiguous(), pb[idx].contiguous(), y[idx].contiguous()
+                bw = w[idx].contiguous() if w is not None else None
+                loss = self.gradient(vec, bpa, bpb, by, bw)
+                self.step += 1
+                mk.adam_step_raw(self.params.data_ptr(), self.grad.data_ptr(), self.m.data_ptr(), self.v.data_ptr(),
+                                 self.n, lr, 0.9, 0.999, 1e-8, self.step, 1.0 / len(idx), _stream_ptr(None))
+                tot += float(loss.item())
+            history.append(tot / n)
+            if log:
+                log("epoch %d loss %.5f" % (ep, history[-1]))
+        return history
+
+    def forward(self, vec, pa, pb):
+        """FP32 logits (mk_mlp_forward)."""
+        B = len(pa)
+        out = torch.empty(B, dtype=torch.float32, device=self.dev)
+        ws = torch.empty(mk.mlp_workspace_size(B, self.H), dtype=torch.uint8, device=self.dev)
+        mk.mlp_forward_raw(self.params.data_ptr(), self.F, self.H, vec.data_ptr(), pa.data_ptr(), pb.data_ptr(), B,
+                           out.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(None))
+        return out
+
+    def score(self, vec, pa, pb, batch=65536):
+        """BF16 tensor-core logits for many pairs (mk_mlp_infer_bf16)."""
+        n = len(pa)
+        out = torch.empty(n, dtype=torch.float32, device=self.dev)
+        ws = torch.empty(mk.mlp_infer_workspace_size(min(batch, max(n, 1)), self.F, self.H), dtype=torch.uint8,
+                         device=self.dev)
+        for s in range(0, n, batch):
+            e = min(n, s + batch)
+            mk.mlp_infer_bf16_raw(self.params.data_ptr(), self.F, self.H, vec.data_ptr(), pa[s:e].data_ptr(),
+                                  pb[s:e].data_ptr(), e - s, out[s:].data_ptr(), ws.data_ptr(), ws.numel(),
+                                  _stream_ptr(None))
+        return out
+
+
+def exact_split_search(texts, pa, pb, frames_per_n=1 << 20, seed=4, chunk=8192, device="cuda"):
+    """The exact judge: mk_separate over every frame of 1..5 worlds, then
+    ``frames_per_n`` sampled relations at 6, 7 and 8 worlds.  Returns (split
+    keys, evaluations spent per pair up to its split or to the end)."""
+    keys = np.empty(len(pa), np.uint64)
+    evals = np.empty(len(pa), np.float64)
+    for s in range(0, len(pa), chunk):
+        e = min(len(pa), s + chunk)
+        pairs = [(texts[a], texts[b]) for a, b in zip(pa[s:e], pb[s:e])]
+        job = SeparateJob(pairs, 1, 5, 6, 8, frames_per_n=frames_per_n, seed=seed, device=device)
+        k = job.run()
+        keys[s:e] = k
+        for i in range(e - s):
+            nv = max(int(job.pa[i]["nvars"]), int(job.pb[i]["nvars"]))
+            evals[s + i] = _evals_to_split(int(k[i]), nv, frames_per_n)
+    return keys, evals
+
+
+def _evals_to_split(key, k, frames_per_n):
+    """Pair evaluations (frame x valuation) the search spends up to and
+    including the first split, or all of them if there is none."""
+    tot = 0
+    last_n = 8 if key == mk.NO_KEY else mk.split_n(key)
+    f = None if key == mk.NO_KEY else (key >> 24) & ((1 << 36) - 1)
+    for n in range(1, 9):
+        frames = (1 << (n * n)) if n <= 5 else frames_per_n
+        vals = n_valuations(k, n, 0)
+        if key != mk.NO_KEY and n == last_n:
+            tot += (f + 1) * vals
+            break
+        tot += frames * vals
+    return float(tot)
+
+
+def identical_pairs(bits_np, pa, pb):
+    """Pairs whose truth vectors are equal (only these can agree on every
+    frame of at most five worlds: the models have n <= 5)."""
+    return np.all(bits_np[pa] == bits_np[pb], axis=1)
+
+
+def budget_walk(texts, pa, pb, order, budget, frames_per_n=1 << 20, chunk=4096, max_pairs=1_000_000, seed=4,
+                log=None):
+    """Check ranked pairs with the exact search, in rank order, until the
+    exact-evaluation budget is spent (or max_pairs pairs are checked).
+    A hit is a pair whose first split is at 6-8 worlds -- it agrees on every
+    frame of at most five worlds -- and whose split certificate mk_certify
+    accepts.  Returns a dict of counts."""
+    spent, checked, hits, certified, late_keys = 0.0, 0, 0, 0, []
+    by_n = np.zeros(9, np.int64)
+    pos = 0
+    while pos < min(len(order), max_pairs) and spent < budget:
+        idx = order[pos:pos + chunk]
+        pos += len(idx)
+        keys, ev = exact_split_search(texts, pa[idx], pb[idx], frames_per_n=frames_per_n, seed=seed)
+        cum = spent + np.cumsum(ev)
+        take = int(np.searchsorted(cum, budget, side="right"))
+        take = min(take, len(idx))
+        for i in range(take):
+            key = int(keys[i])
+            n = mk.split_n(key)
+            by_n[n] += 1
+            if n >= 6:
+                hits += 1
+                a, b = texts[pa[idx[i]]], texts[pb[idx[i]]]
+                c = mk.split_cert(mk.compile(a), mk.compile(b), a, b, seed, 0, None, key)
+                certified += mk.certify_struct(c) == 1
+                late_keys.append((int(idx[i]), key))
+        spent = float(cum[take - 1]) if take else spent
+        checked += take
+        if take < len(idx):
+            break
+        if log:
+            log("  checked %d pairs, %.3g evals, %d late splits" % (checked, spent, hits))
+    return {"pairs_checked": checked, "evals": spent, "late_splits": hits, "certified": certified,
+            "certified_per_1e12_evals": certified / (spent / 1e12) if spent else 0.0,
+            "first_split_n_hist": by_n.tolist(), "hits": late_keys}
+
+
+def proposal_experiment(n_formulas=10000, universe=5_467_766, k=1024, train_identical=100_000,
+                        train_other=100_000, budget=5e13, frames_per_n=1 << 20, epochs=8, seed=5,
+                        train_seed=55, methods=("mlp", "random", "pca10"), log=None, device="cuda"):
+    """The learned proposal against random and PCA-10 rankings at an equal
+    exact-evaluation budget (Sec. 9's retrieval protocol with a learned
+    ranker).  Every number comes from libmk kernels; torch only holds
+    buffers (and computes the PCA-10 comparator's projection)."""
+    import time
+    t0 = time.time()
+    say = log or (lambda *a: None)
+    texts = workloads.proposal_formulas(seed, n_formulas)
+    bits = truth_vectors(texts, seed=seed, device=device)
+    bits_np = bits.cpu().numpy().view(np.uint32)
+    nbr, _ = hamming_knn(bits, k)
+    pa, pb = knn_universe(nbr, universe, seed)
+    say("test universe: %d pairs (%.1f s)" % (len(pa), time.time() - t0))
+
+    # training pairs from a disjoint corpus, labelled by the exact search
+    ttexts = workloads.proposal_formulas(train_seed, n_formulas)
+    tbits = truth_vectors(ttexts, seed=seed, device=device)
+    tbits_np = tbits.cpu().numpy().view(np.uint32)
+    tnbr, _ = hamming_knn(tbits, k)
+    tpa, tpb = knn_universe(tnbr, universe, train_seed)
+    test_set = set(texts)
+    keep = np.array([not (ttexts[a] in test_set and ttexts[b] in test_set) for a, b in zip(tpa, tpb)])
+    tpa, tpb = tpa[keep], tpb[keep]
+    same = identical_pairs(tbits_np, tpa, tpb)
+    rng = np.random.default_rng(train_seed)
+    si = np.where(same)[0]
+    so = np.where(~same)[0]
+    si = rng.choice(si, min(train_identical, len(si)), replace=False)
+    so = rng.choice(so, min(train_other, len(so)), replace=False)
+    keys, _ = exact_split_search(ttexts, tpa[si], tpb[si], frames_per_n=frames_per_n, seed=train_seed)
+    late = np.array([mk.split_n(x) >= 6 for x in keys])
+    # pairs with different truth vectors split on a model of <= 5 worlds: label 0
+    la = np.concatenate([tpa[si], tpa[so]]).astype(np.int32)
+    lb = np.concatenate([tpb[si], tpb[so]]).astype(np.int32)
+    y = np.concatenate([late.astype(np.float32), np.zeros(len(so), np.float32)])
+    npos = int(y.sum())
+    wpos = min(1000.0, (len(y) - npos) / max(1, npos))
+    wt = np.where(y > 0, wpos, 1.0).astype(np.float32)
+    say("training pairs: %d (%d identical-vector, %d late splits) (%.1f s)" % (len(y), len(si), npos,
+                                                                            time.time() - t0))
+    dev = torch.device(device)
+    F = bits.shape[1] * 64
+    net = MLP(F, 256, seed=seed, device=device)
+    hist = net.train(tbits, torch.from_numpy(la).to(dev), torch.from_numpy(lb).to(dev),
+                     torch.from_numpy(y).to(dev), torch.from_numpy(wt).to(dev), epochs=epochs, batch=4096,
+                     lr=1e-3, seed=seed, log=say)
+    say("trained (%.1f s)" % (time.time() - t0))
+
+    # rankings of the test universe
+    dpa, dpb = torch.from_numpy(pa).to(dev), torch.from_numpy(pb).to(dev)
+    orders = {}
+    if "mlp" in methods:
+        s = net.score(bits, dpa, dpb)
+        orders["mlp"] = torch.argsort(s, descending=True, stable=True).cpu().numpy()
+    if "random" in methods:
+        orders["random"] = np.random.default_rng(seed + 1).permutation(len(pa))
+    if "pca10" in methods:
+        xf = torch.from_numpy(np.unpackbits(bits_np.view(np.uint8), axis=1, bitorder="little").astype(np.float32)).to(dev)
+        xf = xf - xf.mean(0, keepdim=True)
+        _, _, V = torch.pca_lowrank(xf, q=10, center=False, niter=4)
+        emb = xf @ V[:, :10]
+        d = ((emb[dpa.long()] - emb[dpb.long()]) ** 2).sum(1)
+        orders["pca10"] = torch.argsort(d, stable=True).cpu().numpy()
+    out = {"universe": len(pa), "train_pairs": len(y), "train_late": npos, "loss_history": hist,
+           "identical_in_universe": int(identical_pairs(bits_np, pa, pb).sum()), "budget_evals": budget}
+    for m, order in orders.items():
+        r = budget_walk(texts, pa, pb, order, budget, frames_per_n=frames_per_n, seed=4)
+        r.pop("hits")
+        out[m] = r
+        say("%s: %s (%.1f s)" % (m, r, time.time() - t0))
+    return out

@@ -72,6 +72,7 @@ class mk_plan_info(ctypes.Structure):
 
 
 JOB_DTYPE = np.dtype([("prog", "<i4"), ("cls", "u1"), ("n_max", "u1"), ("reserved", "<u2")])
+MODEL_DTYPE = np.dtype([("frame", "<u8"), ("val", "<u4"), ("n", "u1"), ("world", "u1"), ("reserved", "<u2")])
 
 
 class mk_separate_cfg(ctypes.Structure):
@@ -125,6 +126,29 @@ _SIGS = {
                                         ctypes.POINTER(mk_plan_info), ctypes.c_uint32, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                         ctypes.c_void_p]),
+    "mk_fingerprint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "mk_knn_workspace_size": (ctypes.c_size_t, [ctypes.c_int32]),
+    "mk_hamming_knn": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                      ctypes.c_void_p]),
+    "mk_mlp_param_count": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32]),
+    "mk_mlp_workspace_size": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32]),
+    "mk_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "mk_mlp_train_workspace_size": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "mk_mlp_gradient": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_size_t, ctypes.c_void_p]),
+    "mk_adam_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_size_t, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_int32, ctypes.c_float, ctypes.c_void_p]),
+    "mk_mlp_infer_workspace_size": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "mk_mlp_infer_bf16": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "mk_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mk_status_error": (ctypes.c_int, [ctypes.c_int32]),
     "mk_version": (ctypes.c_int, []),
@@ -264,7 +288,23 @@ def decode_split(key):
     """Separation key -> (n, frame or sample, valuation, world)."""
     if key == NO_KEY:
         return None
-    return (key >> 60, (key >> 24) & ((1 << 36) - 1), (key >> 3) & ((1 << 21) - 1), key & 7)
+    return (split_n(key), (key >> 24) & ((1 << 36) - 1), (key >> 3) & ((1 << 21) - 1), key & 7)
+
+
+def split_n(key):
+    """Worlds of the split a separation key encodes (0 for no split)."""
+    key = int(key)
+    return 0 if key == NO_KEY else ((key >> 60) & 7) + 1
+
+
+def split_sampled(key):
+    """True if the split was found on a sampled relation (not a K index)."""
+    return int(key) != NO_KEY and bool(int(key) >> 63)
+
+
+def split_key(sampled, n, f, x, w):
+    """The separation key mk_separate writes for a split."""
+    return (int(bool(sampled)) << 63) | ((n - 1) << 60) | (f << 24) | (x << 3) | w
 
 
 # ------------------------------------------------------- certificates
@@ -377,3 +417,56 @@ def census_uneven_raw(d_progs, d_jobs, njobs, d_plan, info, samples, d_samples, 
                       ws_bytes, stream):
     _check(lib().mk_census_uneven(d_progs, d_jobs, njobs, d_plan, ctypes.byref(info), samples, d_samples,
                                   d_out, d_status, d_ws, ws_bytes, stream), "mk_census_uneven")
+
+
+# ------------------------------------------------------- learned proposal
+
+def fingerprint_raw(d_progs, nprog, d_models, group_n, d_bits, d_status, stream):
+    g = np.ascontiguousarray(np.asarray(group_n, np.int32))
+    _check(lib().mk_fingerprint(d_progs, nprog, d_models, g.ctypes.data_as(ctypes.c_void_p), len(g), d_bits,
+                                d_status, stream), "mk_fingerprint")
+
+
+def knn_workspace_size(nvec):
+    return int(lib().mk_knn_workspace_size(nvec))
+
+
+def hamming_knn_raw(d_bits, nvec, words, k, d_nbr, d_dist, d_ws, ws_bytes, stream):
+    _check(lib().mk_hamming_knn(d_bits, nvec, words, k, d_nbr, d_dist, d_ws, ws_bytes, stream), "mk_hamming_knn")
+
+
+def mlp_param_count(features, hidden):
+    return int(lib().mk_mlp_param_count(features, hidden))
+
+
+def mlp_forward_raw(d_params, features, hidden, d_vec, d_pa, d_pb, batch, d_logits, d_ws, ws_bytes, stream):
+    _check(lib().mk_mlp_forward(d_params, features, hidden, d_vec, d_pa, d_pb, batch, d_logits, d_ws, ws_bytes,
+                                stream), "mk_mlp_forward")
+
+
+def mlp_workspace_size(batch, hidden):
+    return int(lib().mk_mlp_workspace_size(batch, hidden))
+
+
+def mlp_train_workspace_size(batch, features, hidden):
+    return int(lib().mk_mlp_train_workspace_size(batch, features, hidden))
+
+
+def mlp_gradient_raw(d_params, features, hidden, d_vec, d_pa, d_pb, d_y, d_w, batch, d_grad, d_loss, d_ws,
+                     ws_bytes, stream):
+    _check(lib().mk_mlp_gradient(d_params, features, hidden, d_vec, d_pa, d_pb, d_y, d_w, batch, d_grad, d_loss,
+                                 d_ws, ws_bytes, stream), "mk_mlp_gradient")
+
+
+def adam_step_raw(d_params, d_grad, d_m, d_v, n, lr, beta1, beta2, eps, step, grad_scale, stream):
+    _check(lib().mk_adam_step(d_params, d_grad, d_m, d_v, n, lr, beta1, beta2, eps, step, grad_scale, stream),
+           "mk_adam_step")
+
+
+def mlp_infer_workspace_size(batch, features, hidden):
+    return int(lib().mk_mlp_infer_workspace_size(batch, features, hidden))
+
+
+def mlp_infer_bf16_raw(d_params, features, hidden, d_vec, d_pa, d_pb, batch, d_logits, d_ws, ws_bytes, stream):
+    _check(lib().mk_mlp_infer_bf16(d_params, features, hidden, d_vec, d_pa, d_pb, batch, d_logits, d_ws, ws_bytes,
+                                   stream), "mk_mlp_infer_bf16")

@@ -246,26 +246,64 @@ def separation_pairs(seed=4, count=1024):
     return out[:count]
 
 
+def context_word_formulas(max_nodes=21, max_depth=10):
+    """Every distinct C^m b: a modal context word C over {[], <>} of length
+    1-3 iterated m >= 1 times over a base b in {T, F, p0, ~p0}, with modal
+    depth <= max_depth and at most max_nodes nodes (the active-synthesis and
+    mining families of Sec. 7), in a fixed order."""
+    out, seen = [], set()
+    words = [""]
+    for _ in range(3):
+        words = [w + c for w in words for c in ("[]", "<>")] + words
+    words = sorted({w for w in words if w}, key=lambda w: (len(w), w))
+    for C in words:
+        cl = len(C) // 2
+        for b in ("T", "F", "p0", "~p0"):
+            bn = 2 if b == "~p0" else 1
+            m = 1
+            while cl * m <= max_depth and cl * m + bn <= max_nodes:
+                t = C * m + b
+                if t not in seen:
+                    seen.add(t)
+                    out.append(t)
+                m += 1
+    return out
+
+
 def proposal_formulas(seed=5, count=10000, bases=2000):
-    """Retrieval corpus: ``bases`` base formulas (length <= 21, depth <= 10,
-    0-2 variables) and Boolean compositions (&, |, -> of two bases, or ~)."""
+    """Retrieval corpus, like the paper's corpus of representatives of
+    sizes 1-21 and modal depths 0-10, most with a Boolean connective (Sec. 9):
+    ``bases`` base formulas -- every iterated modal context word over T, F,
+    p0, ~p0 (context_word_formulas), then random trees (length 2-21, depth
+    0-10, variable-free with probability 0.6, else over p0) -- and Boolean
+    compositions (&, |, -> of two bases, or ~).  Duplicate texts are
+    skipped.  At most one variable keeps every exact check at 6-8 worlds
+    affordable (2^n valuations)."""
     rng = random.Random(seed)
-    base = []
-    for i in range(bases):
+    base = context_word_formulas()[:bases]
+    seen = set(base)
+    tries = 0
+    while len(base) < bases and tries < 100 * bases:
+        tries += 1
         L = rng.randint(2, 21)
         d = rng.randint(0, min(10, L - 1))
-        k = rng.randint(0, 2)
-        base.append(random_formula(rng, L, d, k))
+        k = 0 if rng.random() < 0.6 else 1
+        t = random_formula(rng, L, d, k, const_p=0.3)
+        if t not in seen:
+            seen.add(t)
+            base.append(t)
     out = list(base)
-    while len(out) < count:
-        r = rng.random()
+    tries = 0
+    while len(out) < count and tries < 100 * count:
+        tries += 1
         a = rng.choice(base)
-        if r < 0.1:
-            out.append("~(" + a + ")")
+        if rng.random() < 0.1:
+            t = "~(" + a + ")"
         else:
-            b = rng.choice(base)
-            op = rng.choice(["&", "|", "->"])
-            out.append("(" + a + ") " + op + " (" + b + ")")
+            t = "(" + a + ") " + rng.choice(["&", "|", "->"]) + " (" + rng.choice(base) + ")"
+        if t not in seen:
+            seen.add(t)
+            out.append(t)
     return out
 
 
@@ -273,3 +311,35 @@ def nodes(text):
     """Node count |phi| of a generated text (atoms, constants, operators)."""
     import re
     return len(re.findall(r"p\d+|[pqrs](?!\d)|T|F|~|\[\]|<>|&|\||->", text))
+
+
+def pointed_models(seed=5, counts=(32, 96, 640, 1280, 2048)):
+    """Seeded pointed models for truth vectors: counts[n-1] models on n
+    worlds (each a multiple of 32, so every group of 32 has one n), with a
+    per-model edge probability in [0.1, 0.6], uniform valuations of four
+    variables and a uniform pointed world; drawn from the SplitMix64 stream
+    (seed, tag 3, n).  Returns (models as a record array in mk_model layout,
+    the n of every 32-model group)."""
+    dtype = np.dtype([("frame", "<u8"), ("val", "<u4"), ("n", "u1"), ("world", "u1"), ("reserved", "<u2")])
+    out, groups = [], []
+    for n, cnt in enumerate(counts, start=1):
+        assert cnt % 32 == 0
+        st = splitmix_state(seed, 3, n)
+        j = 0
+        for _ in range(cnt):
+            d = [splitmix_out(st, j + i) for i in range(3)]
+            j += 3
+            p = 0.1 + 0.5 * ((d[0] >> 11) / float(1 << 53))
+            frame = 0
+            r = d[1]
+            for e in range(n * n):
+                if e % 16 == 0 and e:
+                    r = splitmix_out(st, j)
+                    j += 1
+                if ((r >> (4 * (e % 16))) & 0xF) < int(p * 16):
+                    frame |= 1 << e
+            val = d[2] & ((1 << (4 * n)) - 1)
+            world = (d[2] >> 40) % n
+            out.append((frame, val, n, world, 0))
+        groups += [n] * (cnt // 32)
+    return np.array(out, dtype=dtype), np.array(groups, np.int32)

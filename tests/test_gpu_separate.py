@@ -29,7 +29,7 @@ def oracle_first_split(a, b, sizes, samples_table=None):
         r = oracle.pair_layer(a, b, n, samples=None if samples_table is None else samples_table[n])
         if r["split"]:
             f, v, w, _, _ = r["split"]
-            return (n << 60) | (f << 24) | (v << 3) | w
+            return mk.split_key(False, n, f, v, w)
     return mk.NO_KEY
 
 
@@ -81,7 +81,7 @@ def test_sampled_relations_first_split():
                 r = oracle.pair_sampled(a, b, n, 11, 0, 100000)
                 if r["split"]:
                     s, v, w, _, _ = r["split"]
-                    want = (n << 60) | (s << 24) | (v << 3) | w
+                    want = mk.split_key(True, n, s, v, w)
                     break
         assert int(got[i]) == want, (a, b)
         if want != mk.NO_KEY:
@@ -92,3 +92,23 @@ def test_equivalent_pair_never_splits():
     pairs = [("[][]T", "T"), ("<>F", "F"), ("~<>~T", "T"), ("p | ~p", "T")]
     job = engine().SeparateJob(pairs, 1, 5, 7, 7, frames_per_n=50000, seed=1)
     assert all(int(k) == mk.NO_KEY for k in job.run())
+
+
+def test_sampled_six_world_split_certifies():
+    # a split found on a sampled 6-world relation carries the sampled flag,
+    # decodes to that relation and certifies (sampled sizes may include 6)
+    pairs = [("<><><>T", "<><><><>T"), (W.alpha(1), W.alpha(2)), ("[][][]F", "[][][][]F")]
+    job = engine().SeparateJob(pairs, 1, 2, 6, 7, frames_per_n=200000, seed=13)
+    got = job.run()
+    for i, (a, b) in enumerate(pairs):
+        want = mk.NO_KEY
+        for n in (6, 7):
+            r = oracle.pair_sampled(a, b, n, 13, 0, 200000)
+            if r["split"]:
+                s, v, w, _, _ = r["split"]
+                want = mk.split_key(True, n, s, v, w)
+                break
+        assert int(got[i]) == want, (a, b)
+        if want != mk.NO_KEY:
+            assert mk.split_sampled(got[i]) and mk.split_n(got[i]) in (6, 7)
+            assert mk.certify_struct(job.certificate(i, got[i])) == 1
