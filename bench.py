@@ -39,6 +39,10 @@ S = 256
 SMS = 152
 SM_MAX_MHZ = 2070.0
 LOP3_PER_SM_CLK = 64        # 3-input logic ops per SM per clock (4 SMSPs x 16 ALU lanes)
+# DRAM bytes (read + write) of census_layer_kernel<5, 8, 256> per formula of
+# a K n=5 launch: 74,752 B for the 16-formula ncu capture of this kernel
+# (bench.py --profile-case census5:16), scaled by the formulas processed.
+DRAM_BYTES_PER_FORMULA_K5 = 74752 / 16
 
 
 def parse():
@@ -322,7 +326,8 @@ def run_mk(args):
                       "parallelism": "replicas x%d (independent batches)" % world},
            "roofline": {"bound": "alu", "kernel": "census_layer_kernel<5> (K, n=5)",
                         "achieved": achieved, "peak": peak_tops, "unit": "Tops/s (3-input logic ops)",
-                        "frac": achieved / peak_tops, "traffic": None,
+                        "frac": achieved / peak_tops, "traffic": DRAM_BYTES_PER_FORMULA_K5 * nprog,
+                        "traffic_note": "bytes per launch, scaled from a 16-formula ncu capture",
                         "algorithmic_ops_per_launch": ops_dom, "launch_ms": dom_ms,
                         "peak_basis": "%d SMs x %d logic ops/clk x %.0f MHz" % (sms, LOP3_PER_SM_CLK, SM_MAX_MHZ),
                         "calibrated_lop3_tops": cal_tops},

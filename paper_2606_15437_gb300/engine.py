@@ -613,3 +613,44 @@ def proposal_experiment(n_formulas=10000, universe=5_467_766, k=1024, train_iden
         out[m] = r
         say("%s: %s (%.1f s)" % (m, r, time.time() - t0))
     return out
+
+
+# ------------------------------------------------------------ sharding
+
+def shard_range(total, rank, world):
+    """[lo, hi) of the rank-th of ``world`` near-equal contiguous shards of
+    [0, total) (frame K indices for the census, pairs for separation)."""
+    lo = total * rank // world
+    hi = total * (rank + 1) // world
+    return lo, hi
+
+
+def merge_results(parts):
+    """Merge census results of disjoint frame shards: counts add, the
+    witness is the least key (the census's own reduction, Sec. 4)."""
+    parts = [np.asarray(p, np.uint64) for p in parts]
+    out = parts[0].copy()
+    for p in parts[1:]:
+        out[..., 0] += p[..., 0]
+        out[..., 1] += p[..., 1]
+        out[..., 2] = np.minimum(out[..., 2], p[..., 2])
+    return out
+
+
+def allreduce_results(res, group=None):
+    """The same merge across ranks with torch.distributed (sum of the
+    counts, min of the keys; a missing witness, all ones, maps to the
+    largest int64 for the min)."""
+    import torch.distributed as dist
+    r = np.asarray(res, np.uint64)
+    counts = torch.from_numpy(r[..., :2].astype(np.int64).copy())
+    keys = r[..., 2].copy()
+    none = keys == np.uint64(mk.NO_KEY)
+    k64 = torch.from_numpy(np.where(none, np.int64(2 ** 63 - 1), keys.astype(np.int64)))
+    dist.all_reduce(counts, op=dist.ReduceOp.SUM, group=group)
+    dist.all_reduce(k64, op=dist.ReduceOp.MIN, group=group)
+    out = np.empty_like(r)
+    out[..., :2] = counts.numpy().astype(np.uint64)
+    k = k64.numpy()
+    out[..., 2] = np.where(k == 2 ** 63 - 1, np.uint64(mk.NO_KEY), k.astype(np.uint64))
+    return out
