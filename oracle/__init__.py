@@ -54,6 +54,15 @@ class _Pair(ctypes.Structure):
                 ("frames_disagree", ctypes.c_uint64)]
 
 
+class _Stress(ctypes.Structure):
+    _fields_ = [("found", ctypes.c_int32), ("nvals", ctypes.c_int32), ("s", ctypes.c_uint64),
+                ("x", ctypes.c_uint32), ("w", ctypes.c_uint32), ("nsplit", ctypes.c_uint64)]
+
+
+NUM_TEMPLATES = 39
+GENERATORS = ("er", "flip", "scc", "deadend", "backedge", "permscc")
+
+
 def _load():
     global _lib
     with _lock:
@@ -75,6 +84,9 @@ def _load():
             lib.orc_stream_state.argtypes = [u64, u64, u64]
             lib.orc_stream_state.restype = u64
             lib.orc_frame_valid_all.argtypes = [cs, i32, p]
+            lib.orc_template.argtypes = [i32, i32, p]
+            lib.orc_stress_relation.argtypes = [i32, u64, i32, u64, p]
+            lib.orc_stress_pair.argtypes = [cs, cs, i32, p, u64, ctypes.POINTER(_Stress)]
             lib.orc_nvars.argtypes = [cs]
             lib.orc_nodes.argtypes = [cs]
             _lib = lib
@@ -198,3 +210,44 @@ def frame_matrix(f, n):
 
 def threads():
     return int(_load().orc_threads())
+
+
+def template(tid, n):
+    """Successor masks (list of n ints) of stress template ``tid`` on n worlds."""
+    out = (ctypes.c_uint32 * 16)()
+    rc = _load().orc_template(int(tid), int(n), out)
+    if rc:
+        raise ValueError("orc_template(%d, %d) = %d" % (tid, n, rc))
+    return [int(out[w]) for w in range(n)]
+
+
+def stress_relation(gen, seed, n, s):
+    """Successor masks of relation ``s`` of adversarial generator ``gen``."""
+    g = GENERATORS.index(gen) if isinstance(gen, str) else int(gen)
+    out = (ctypes.c_uint32 * 16)()
+    rc = _load().orc_stress_relation(g, int(seed), int(n), int(s), out)
+    if rc:
+        raise ValueError("orc_stress_relation(%d, %d, %d) = %d" % (g, n, s, rc))
+    return [int(out[w]) for w in range(n)]
+
+
+def stress_relations(gen, seed, n, first, count):
+    """uint32 array [count, 16] of successor masks (rows >= n are zero)."""
+    a = np.zeros((count, 16), np.uint32)
+    for i in range(count):
+        a[i, :n] = stress_relation(gen, seed, n, first + i)
+    return a
+
+
+def stress_pair(phi, psi, n, succ):
+    """First split of (phi, psi) over the relations ``succ`` ([count, 16]
+    successor masks), in (relation, valuation, world) order, and the number
+    of relations on which they differ."""
+    a = np.ascontiguousarray(np.asarray(succ, dtype=np.uint32).reshape(-1, 16))
+    o = _Stress()
+    rc = _load().orc_stress_pair(phi.encode(), psi.encode(), int(n),
+                                 a.ctypes.data_as(ctypes.c_void_p), len(a), ctypes.byref(o))
+    if rc:
+        raise ValueError("orc_stress_pair rc=%d" % rc)
+    split = (int(o.s), int(o.x), int(o.w)) if o.found else None
+    return {"split": split, "nsplit": int(o.nsplit), "nvals": int(o.nvals)}

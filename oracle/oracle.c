@@ -24,6 +24,9 @@
  *                 witness -- the outputs of the corpus scan of Alg. 1 (Sec. 4)
  *   separation    the least (n, frame, valuation, world) at which phi and
  *                 psi take different truth values (Def. 2, Prop. 4, Sec. 7)
+ *   large frames  the stress templates and adversarial relation generators
+ *                 of Sec. 7 / Table 2 on up to 16 worlds, and the same
+ *                 separation order over an explicit list of relations
  *
  * Readings of the paper where it is silent (each is listed in the design doc):
  *   - frame index f of an n-world frame: R(w,v) is bit (w*n+v) of f
@@ -485,3 +488,272 @@ int orc_frame_valid_all(const char *text, int n, uint8_t *valid) {
 int orc_in_class(int cls, int n, const uint8_t *R) { return in_class(cls, n, R); }
 
 int orc_threads(void) { return omp_get_max_threads(); }
+
+/* ================================================ large frames (Sec. 7)
+ *
+ * Separation beyond the exhaustive sizes runs over explicit relations on
+ * n <= 16 worlds: the named stress templates (paths, reverse paths, loops,
+ * forks, cycles, stars, sparse and dense frames) and the adversarial relation
+ * generators of Table 2.  The paper names these families without fixing a
+ * construction; the readings below are the ones this project uses (each is
+ * listed in the design doc).  A relation is returned as successor masks:
+ * bit v of succ[w] is set iff R(w, v).
+ */
+
+#define ORC_STRESS_MAX 16
+#define ORC_NUM_TEMPLATES 39
+
+static void rel_clear(int n, uint8_t *R) { memset(R, 0, (size_t)n * n); }
+static void rel_add(int n, uint8_t *R, int w, int v) { if (w >= 0 && w < n && v >= 0 && v < n) R[w * n + v] = 1; }
+static void rel_to_succ(int n, const uint8_t *R, uint32_t *succ) {
+    for (int w = 0; w < n; w++) {
+        succ[w] = 0;
+        for (int v = 0; v < n; v++) if (R[w * n + v]) succ[w] |= 1u << v;
+    }
+}
+
+/* forks: branch 0 -> 1 -> ... -> b and branch 0 -> b+1 -> ... -> n-1 */
+static void fork_rel(int n, int b, uint8_t *R) {
+    for (int i = 0; i < b && i + 1 < n; i++) rel_add(n, R, i, i + 1);
+    if (b + 1 < n) rel_add(n, R, 0, b + 1);
+    for (int i = b + 1; i + 1 < n; i++) rel_add(n, R, i, i + 1);
+}
+
+/* the fixed sparse / dense templates: byte (e mod 8) of output e/8 of the
+   SplitMix64 stream (seed 0x5EED, tag 40 + variant, n) decides edge e */
+static void coin_rel(int n, int variant, int thresh, uint8_t *R) {
+    uint64_t st = orc_stream_state(0x5EED, 40 + (uint64_t)variant, (uint64_t)n);
+    for (int e = 0; e < n * n; e++) {
+        uint64_t d = orc_splitmix_out(st, (uint64_t)(e / 8));
+        if ((int)((d >> (8 * (e % 8))) & 0xFFu) < thresh) R[e] = 1;
+    }
+}
+
+/* Template `id` (0 .. 38) on n worlds, as a 0/1 matrix.  h = n/2 rounded
+   down, c = n/2 rounded up. */
+static int template_rel(int id, int n, uint8_t *R) {
+    int h = n / 2, c = (n + 1) / 2, w, v;
+    rel_clear(n, R);
+    switch (id) {
+    case 0: for (w = 0; w + 1 < n; w++) rel_add(n, R, w, w + 1); break;                 /* path */
+    case 1: for (w = 0; w + 1 < n; w++) rel_add(n, R, w + 1, w); break;                 /* reverse path */
+    case 2: for (w = 0; w < n; w++) { rel_add(n, R, w, w); rel_add(n, R, w, w + 1); } break; /* reflexive path */
+    case 3: for (w = 0; w + 1 < n; w++) rel_add(n, R, w, w + 1); rel_add(n, R, n - 1, n - 1); break; /* looped path */
+    case 4: for (w = 0; w + 1 < n; w++) rel_add(n, R, w, w + 1); rel_add(n, R, 0, 0); break;  /* rooted loop */
+    case 5: for (w = 0; w < n; w++) for (v = w + 1; v < n; v++) rel_add(n, R, w, v); break;  /* strict order */
+    case 6: for (w = 0; w < n; w++) for (v = w; v < n; v++) rel_add(n, R, w, v); break;      /* preorder chain */
+    case 7: for (w = 0; w < n; w++) rel_add(n, R, w, (w + 1) % n); break;                   /* cycle */
+    case 8: for (w = 0; w < n; w++) rel_add(n, R, (w + 1) % n, w); break;                   /* reverse cycle */
+    case 9: for (w = 0; w < n; w++) { rel_add(n, R, w, (w + 1) % n); rel_add(n, R, w, w); } break;
+    case 10: for (w = 0; w < n; w++) { rel_add(n, R, w, (w + 1) % n); rel_add(n, R, (w + 1) % n, w); } break;
+    case 11: for (w = 0; w + 1 < n; w++) { rel_add(n, R, w, w + 1); rel_add(n, R, w + 1, w); } break;
+    case 12: for (v = 1; v < n; v++) rel_add(n, R, 0, v); break;                            /* out-star */
+    case 13: for (v = 1; v < n; v++) rel_add(n, R, v, 0); break;                            /* in-star */
+    case 14: for (v = 1; v < n; v++) { rel_add(n, R, 0, v); rel_add(n, R, v, 0); } break;
+    case 15: for (v = 1; v < n; v++) rel_add(n, R, 0, v); for (w = 0; w < n; w++) rel_add(n, R, w, w); break;
+    case 16: fork_rel(n, h, R); break;
+    case 17: fork_rel(n, 1, R); break;
+    case 18: fork_rel(n, 2, R); break;
+    case 19: fork_rel(n, n - 2, R); break;
+    case 20: fork_rel(n, h, R); rel_add(n, R, h, h); rel_add(n, R, n - 1, n - 1); break;    /* looped fork */
+    case 21: for (w = 0; w < n; w++) { rel_add(n, R, w, 2 * w + 1); rel_add(n, R, w, 2 * w + 2); } break;
+    case 22: for (w = 0; w < n; w++) { rel_add(n, R, 2 * w + 1, w); rel_add(n, R, 2 * w + 2, w); } break;
+    case 23: for (w = 0; w < n; w++) for (v = 0; v < n; v++) rel_add(n, R, w, v); break;    /* complete */
+    case 24: for (w = 0; w < n; w++) for (v = 0; v < n; v++) if (w != v) rel_add(n, R, w, v); break;
+    case 25: for (w = 0; w < n; w++) rel_add(n, R, w, w); break;                            /* identity */
+    case 26: break;                                                                         /* empty */
+    case 27: for (w = 0; w + 1 < n; w++) rel_add(n, R, w, w + 1); rel_add(n, R, n - 1, h); break; /* lasso */
+    case 28:                                                                                 /* two cycles */
+        for (w = 0; w < h; w++) rel_add(n, R, w, (w + 1) % h);
+        for (w = h; w < n; w++) rel_add(n, R, w, w + 1 < n ? w + 1 : h);
+        if (h >= 1) rel_add(n, R, h - 1, h);
+        break;
+    case 29: case 30: case 31: coin_rel(n, id - 29, 32, R); break;                          /* sparse */
+    case 32: case 33: case 34: coin_rel(n, id - 29, 224, R); break;                         /* dense */
+    case 35: for (w = 0; w + 1 < c; w++) rel_add(n, R, w, w + 1);                           /* comb */
+             for (w = 0; w < n - c; w++) rel_add(n, R, w, c + w);
+             break;
+    case 36: for (w = 0; w < n; w++) { rel_add(n, R, w, w + 1); rel_add(n, R, w, w + 2); } break; /* skip path */
+    case 37: for (w = 0; w + 1 < n; w++) rel_add(n, R, w, w + 1);                           /* half-reflexive path */
+             for (w = 1; w < n; w += 2) rel_add(n, R, w, w);
+             break;
+    case 38: for (w = 0; w < n; w++) for (v = 0; v < w; v++) rel_add(n, R, w, v); break;    /* reverse strict order */
+    default: return -1;
+    }
+    return 0;
+}
+
+int orc_template(int id, int n, uint32_t *succ) {
+    uint8_t R[ORC_STRESS_MAX * ORC_STRESS_MAX];
+    if (n < 1 || n > ORC_STRESS_MAX) return -2;
+    if (template_rel(id, n, R)) return -1;
+    rel_to_succ(n, R, succ);
+    return 0;
+}
+
+/* Adversarial relation generators (Table 2), relation number s of generator
+ * gen at n worlds (2 <= n <= 16; Erdos-Renyi also n = 1):
+ *
+ *   0 Erdos-Renyi    stream tag 2, D = 9 draws per relation for n <= 8 and
+ *                    33 above (so that n <= 8 is the sampled family of
+ *                    orc_sample_frame): t = 26 + floor(hi32(d0) * 103 / 2^32),
+ *                    edge e present iff byte (e mod 8) of d(1 + e/8) < t.
+ *   others           stream tag 16 + gen, D = 40 draws per relation: d0 gives
+ *                    t as above, d1..d32 the edge coins (byte e mod 8 of
+ *                    d(1 + e/8)), d33..d39 the choices c_0..c_27 (16-bit chunk
+ *                    i mod 4 of d(33 + i/4)); r(i, m) = floor(c_i * m / 2^16).
+ *   1 edge flip      template r(0, 39), then 1 + r(1, 4) flips, flip i
+ *                    toggling edge e = r(2 + i, n*n) (in that order).
+ *   2 SCC bottleneck a = 1 + r(0, n-1); blocks [0, a) and [a, n); a block of
+ *                    two or more worlds gets the cycle lo -> lo+1 -> ... ->
+ *                    hi-1 -> lo; every intra-block pair (self-loops included)
+ *                    whose coin is below t is added; one bridge a-1 -> a.
+ *   3 dead ends      the coin relation (edge e iff coin e < t), then
+ *                    1 + r(0, 3) worlds r(1 + i, n) lose every successor.
+ *   4 back edges     the path 0 -> 1 -> ... -> n-1 plus 1 + r(0, 4) edges
+ *                    max(x, y) -> min(x, y), x = r(1 + 2i, n), y = r(2 + 2i, n).
+ *   5 permuted       the SCC-bottleneck relation built from this generator's
+ *     bottleneck     own draws, relabelled by the permutation pi obtained by
+ *                    Fisher-Yates from the identity: for i = n-1 down to 1,
+ *                    swap pi[i] and pi[r(4 + n-1-i, i+1)]; R'(pi(w), pi(v)) =
+ *                    R(w, v).
+ */
+typedef struct { uint64_t st, base; } ogen;
+
+static uint64_t g_draw(const ogen *g, int i) { return orc_splitmix_out(g->st, g->base + (uint64_t)i); }
+static int g_coin(const ogen *g, int e) { return (int)((g_draw(g, 1 + e / 8) >> (8 * (e % 8))) & 0xFFu); }
+static uint32_t g_r(const ogen *g, int i, uint32_t m) {
+    uint32_t c = (uint32_t)((g_draw(g, 33 + i / 4) >> (16 * (i % 4))) & 0xFFFFu);
+    return (uint32_t)(((uint64_t)c * m) >> 16);
+}
+static int g_thresh(const ogen *g) { return 26 + (int)(((g_draw(g, 0) >> 32) * 103ULL) >> 32); }
+
+static void scc_rel(const ogen *g, int n, uint8_t *R) {
+    int a = 1 + (int)g_r(g, 0, (uint32_t)(n - 1)), t = g_thresh(g);
+    int lo[2] = {0, a}, hi[2] = {a, n};
+    rel_clear(n, R);
+    for (int b = 0; b < 2; b++) {
+        if (hi[b] - lo[b] >= 2) {
+            for (int w = lo[b]; w < hi[b]; w++) rel_add(n, R, w, w + 1 < hi[b] ? w + 1 : lo[b]);
+        }
+        for (int w = lo[b]; w < hi[b]; w++)
+            for (int v = lo[b]; v < hi[b]; v++)
+                if (g_coin(g, w * n + v) < t) rel_add(n, R, w, v);
+    }
+    rel_add(n, R, a - 1, a);
+}
+
+int orc_stress_relation(int gen, uint64_t seed, int n, uint64_t s, uint32_t *succ) {
+    uint8_t R[ORC_STRESS_MAX * ORC_STRESS_MAX], Q[ORC_STRESS_MAX * ORC_STRESS_MAX];
+    if (n < 1 || n > ORC_STRESS_MAX || (gen != 0 && n < 2)) return -2;
+    ogen g;
+    rel_clear(n, R);
+    if (gen == 0) {
+        uint64_t D = n <= 8 ? 9 : 33;
+        g.st = orc_stream_state(seed, 2, (uint64_t)n);
+        g.base = D * s;
+        int t = g_thresh(&g);
+        for (int e = 0; e < n * n; e++) if (g_coin(&g, e) < t) R[e] = 1;
+        rel_to_succ(n, R, succ);
+        return 0;
+    }
+    if (gen < 0 || gen > 5) return -1;
+    g.st = orc_stream_state(seed, 16 + (uint64_t)gen, (uint64_t)n);
+    g.base = 40 * s;
+    int t = g_thresh(&g);
+    if (gen == 1) {
+        template_rel((int)g_r(&g, 0, ORC_NUM_TEMPLATES), n, R);
+        int m = 1 + (int)g_r(&g, 1, 4);
+        for (int i = 0; i < m; i++) {
+            int e = (int)g_r(&g, 2 + i, (uint32_t)(n * n));
+            R[e] = (uint8_t)!R[e];
+        }
+    } else if (gen == 2) {
+        scc_rel(&g, n, R);
+    } else if (gen == 3) {
+        for (int e = 0; e < n * n; e++) if (g_coin(&g, e) < t) R[e] = 1;
+        int m = 1 + (int)g_r(&g, 0, 3);
+        for (int i = 0; i < m; i++) {
+            int w = (int)g_r(&g, 1 + i, (uint32_t)n);
+            for (int v = 0; v < n; v++) R[w * n + v] = 0;
+        }
+    } else if (gen == 4) {
+        for (int w = 0; w + 1 < n; w++) rel_add(n, R, w, w + 1);
+        int m = 1 + (int)g_r(&g, 0, 4);
+        for (int i = 0; i < m; i++) {
+            int x = (int)g_r(&g, 1 + 2 * i, (uint32_t)n), y = (int)g_r(&g, 2 + 2 * i, (uint32_t)n);
+            rel_add(n, R, x > y ? x : y, x > y ? y : x);
+        }
+    } else {
+        int pi[ORC_STRESS_MAX];
+        scc_rel(&g, n, Q);
+        for (int i = 0; i < n; i++) pi[i] = i;
+        for (int i = n - 1; i >= 1; i--) {
+            int j = (int)g_r(&g, 4 + (n - 1 - i), (uint32_t)(i + 1));
+            int tmp = pi[i]; pi[i] = pi[j]; pi[j] = tmp;
+        }
+        for (int w = 0; w < n; w++)
+            for (int v = 0; v < n; v++)
+                if (Q[w * n + v]) R[pi[w] * n + pi[v]] = 1;
+    }
+    rel_to_succ(n, R, succ);
+    return 0;
+}
+
+/* Separation over explicit relations: for relations s = 0 .. count-1 (given
+   as successor masks succ[s*16 + w]), valuations x = 0 .. 2^(k n)-1 and
+   worlds w, the least (s, x, w) at which phi and psi differ (the order of
+   Def. 2 with relations in list order), and the number of relations on
+   which they differ at all.  Exhaustive valuations only: k*n <= 16. */
+typedef struct {
+    int32_t found, nvals;
+    uint64_t s;
+    uint32_t x, w;
+    uint64_t nsplit;
+} orc_stress_out;
+
+int orc_stress_pair(const char *phi, const char *psi, int n, const uint32_t *succ, uint64_t count,
+                    orc_stress_out *out) {
+    oform fa, fb;
+    memset(out, 0, sizeof(*out));
+    if (n < 1 || n > ORC_STRESS_MAX) return -2;
+    if (parse(phi, &fa) || parse(psi, &fb)) return -1;
+    int k = fa.nvars > fb.nvars ? fa.nvars : fb.nvars;
+    if (k * n > 16) return -4;
+    uint64_t nval = (uint64_t)1 << (k * n);
+    out->nvals = (int32_t)nval;
+    uint64_t best_s = UINT64_MAX, nsplit = 0;
+    uint32_t best_x = 0, best_w = 0;
+    #pragma omp parallel
+    {
+        uint64_t ls = UINT64_MAX; uint32_t lx = 0, lw = 0;
+        #pragma omp for schedule(dynamic, 16) reduction(+:nsplit)
+        for (int64_t si = 0; si < (int64_t)count; si++) {
+            uint8_t R[ORC_STRESS_MAX * ORC_STRESS_MAX], V[ORC_MAX_VARS * ORC_STRESS_MAX];
+            uint8_t ta[ORC_STRESS_MAX], tb[ORC_STRESS_MAX];
+            for (int w = 0; w < n; w++)
+                for (int v = 0; v < n; v++) R[w * n + v] = (uint8_t)((succ[si * 16 + w] >> v) & 1u);
+            int hit = 0;
+            for (uint64_t x = 0; x < nval && !hit; x++) {
+                decode_val(x, k, n, V);
+                truth(&fa, fa.root, n, R, V, ta);
+                truth(&fb, fb.root, n, R, V, tb);
+                for (int w = 0; w < n; w++) {
+                    if (ta[w] != tb[w]) {
+                        hit = 1;
+                        if ((uint64_t)si < ls) { ls = (uint64_t)si; lx = (uint32_t)x; lw = (uint32_t)w; }
+                        break;
+                    }
+                }
+            }
+            nsplit += (uint64_t)hit;
+        }
+        #pragma omp critical
+        {
+            if (ls < best_s) { best_s = ls; best_x = lx; best_w = lw; }
+        }
+    }
+    out->nsplit = nsplit;
+    if (best_s != UINT64_MAX) { out->found = 1; out->s = best_s; out->x = best_x; out->w = best_w; }
+    return 0;
+}
