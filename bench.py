@@ -56,8 +56,11 @@ def parse():
     ap.add_argument("--profile-case", default=None,
                     help="census5:F -- run the K n=5 layer of the first F five-world formulas twice "
                          "(a warm-up and the launch an ncu capture selects with -s 1 -c 1), then exit; "
-                         "separation:P -- the same for the first P separation pairs at n=6")
-    ap.add_argument("--workload", default="census5", choices=["census5", "uneven", "separation", "learned"],
+                         "separation:P -- the same for the first P separation pairs at n=6; "
+                         "stress:P -- the first P mining candidates on 2^16 16-world relations")
+    ap.add_argument("--relations", type=int, default=1 << 18,
+                    help="relations per generator and size (--workload adversarial)")
+    ap.add_argument("--workload", default="census5", choices=["census5", "uneven", "separation", "learned", "adversarial"],
                     help="census5 (default, the headline): five-world census; uneven: 20,000 formulas "
                          "with their own class and n_max in one persistent graph-launched run; "
                          "separation: 1,024 variable-free pairs through 6 worlds exhaustively, then "
@@ -497,6 +500,61 @@ def run_separation(args):
     print(json.dumps(out), flush=True)
 
 
+def run_adversarial(args):
+    """Large-frame separation (Sec. 7 mining, Table 2): the context-word
+    mining candidates are scanned on every frame of <= 5 worlds and the
+    exact-prefix survivors stressed on the 39 templates at 6..16 worlds;
+    then the survivors plus four early-split controls are scanned on
+    2^18 relations of each adversarial generator at 6, 8, ..., 16 worlds
+    (one-variable pairs through 12 worlds, constant pairs beyond), every
+    pair on every relation and valuation; every first split certified."""
+    import time
+    import torch
+    from paper_2606_15437_gb300 import build as mkbuild
+    from paper_2606_15437_gb300 import engine as E
+    mkbuild.build()
+    log = lambda m: sys.stderr.write(m + "\n")
+    dev = torch.device("cuda", 0)
+    t0 = time.time()
+    mine = E.mine_context_words(log=log)
+    t_mine = time.time() - t0
+    cand = [(r["phi"], r["psi"]) for r in mine if r["a"] == 5]
+    ctrl = [(r["phi"], r["psi"]) for r in mine if r["a"] <= 2][:4]
+    pairs = cand + ctrl
+    late_tpl = sum(1 for r in mine if r["a"] == 5 and r["template"] is not None)
+    E.adversarial_search(pairs, sizes=(6,), relations=1 << 12)          # warm-up
+    clocks = ClockSampler(gpu_smi_id(dev, 0))
+    rows, first = E.adversarial_search(pairs, relations=args.relations, log=log)
+    clk = clocks.stop()
+    gpu_s = sum(r["gpu_s"] for r in rows)
+    evals = sum(r["evals"] for r in rows)
+    ops = sum(r["lop3"] for r in rows)
+    peak = SMS * LOP3_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = ops / gpu_s / 1e12
+    by_gen = {}
+    for r in rows:
+        g = by_gen.setdefault(r["generator"], {"relations": 0, "tests": 0, "evals": 0.0, "split_pairs": 0,
+                                               "certified": 0, "non_template": 0, "gpu_s": 0.0})
+        for k in g:
+            g[k] += r[k]
+    out = {"metric": "G pair-relation-valuation evals/s (bit-exact)", "value": evals / gpu_s / 1e9,
+           "unit": "G evals/s", "n_gpus": 1, "higher_is_better": True, "vs_baseline": None, "dtype": "u32",
+           "data": "synthetic (seeded)",
+           "config": {"workload": "adversarial frame synthesis: %d exact-prefix mining candidates + %d controls "
+                      "x 6 generators x n in {6,8,10,12,14,16} x %d relations each" %
+                      (len(cand), len(ctrl), args.relations),
+                      "mining_candidates": len(mine), "exact_prefix": len(cand),
+                      "late_template_witness": late_tpl, "mining_seconds": t_mine},
+           "roofline": {"bound": "alu", "kernel": "stress_kernel", "achieved": achieved, "peak": peak,
+                        "unit": "Tops/s (3-input logic ops)", "frac": achieved / peak,
+                        "peak_basis": "%d SMs x %d logic ops/clk x %.0f MHz" % (SMS, LOP3_PER_SM_CLK, SM_MAX_MHZ)},
+           "gpu_seconds": gpu_s, "evals": evals, "by_generator": by_gen,
+           "top_mining": [{k: r[k] for k in ("phi", "psi", "a", "template", "J")} for r in mine[:6]],
+           "separated_pairs": sum(1 for f in first if f is not None),
+           "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
 def run_profile_case(spec):
     """Small fixed launches for ncu captures (a warm-up, then the captured one)."""
     import torch
@@ -510,6 +568,16 @@ def run_profile_case(spec):
         job = E.CensusJob(W.census5_formulas()[:count], ("K",), 5, 5, samples=S, seed=SEED)
     elif kind == "separation":
         job = E.SeparateJob(W.separation_pairs(4)[:count], 6, 6, frame_lo=0, frame_hi=1 << 30)
+    elif kind == "stress":
+        pairs = [(a, b) for a, b, _ in W.mining_candidates()[:count]]
+        sj = E.StressJob(pairs)
+        rels = E.RelationSet.generated("er", 6, 16, 0, 1 << 16)
+        idx = np.nonzero(sj.k == 0)[0]          # constant pairs: one valuation per relation
+        sj.run(rels, idx, count_splits=True)
+        sj.run(rels, idx, count_splits=True)
+        torch.cuda.synchronize()
+        print("profile case %s done" % spec)
+        return
     else:
         raise SystemExit("unknown profile case " + spec)
     job.run()
@@ -559,6 +627,8 @@ def main():
         run_separation(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "adversarial":
+        run_adversarial(args)
     else:
         run_mk(args)
 

@@ -393,6 +393,77 @@ int mk_mlp_infer_bf16(const float *d_params, int32_t features, int32_t hidden, c
                       const int32_t *d_pa, const int32_t *d_pb, int32_t batch, float *d_logits,
                       void *d_workspace, size_t ws_bytes, void *stream);
 
+/* ------------------------------------------- large frames (Sec. 7) */
+/* Separation beyond the exhaustive sizes runs over explicit relations on up
+   to 16 worlds: the 39 stress templates (path, reverse-path, reflexive-path,
+   fork, cycle, star, sparse and dense frames) used to challenge pairs that
+   agree on every small frame, and the six adversarial relation generators
+   of Table 2.  The paper names these families without fixing their
+   construction; mk_template and mk_stress_relation define the ones used
+   here (their readings are listed with the design notes).  A relation is a
+   list of successor masks: bit v of succ[w] is set iff R(w, v). */
+#define MK_MAX_WORLDS_STRESS 16
+#define MK_NUM_TEMPLATES 39
+enum {
+    MK_GEN_ER = 0,        /* Erdos-Renyi, per-relation p in [0.1, 0.5]      */
+    MK_GEN_FLIP = 1,      /* 1..4 edge flips of a random template           */
+    MK_GEN_SCC = 2,       /* two strongly connected blocks, one bridge      */
+    MK_GEN_DEADEND = 3,   /* Erdos-Renyi with 1..3 worlds made dead ends    */
+    MK_GEN_BACKEDGE = 4,  /* the path plus 1..4 backward edges              */
+    MK_GEN_PERMSCC = 5,   /* SCC bottleneck with the worlds relabelled      */
+    MK_NUM_GENERATORS = 6
+};
+
+/* Template id (0..38) on n worlds (1..16), host: succ[0..n). */
+int mk_template(int32_t id, int32_t n, uint32_t *succ);
+
+/* Relation s of generator gen on n worlds (host): every relation is a
+   function of (gen, seed, n, s) alone, drawn from SplitMix64 streams; for
+   MK_GEN_ER and n <= 8 it is mk_sample_relation(seed, n, s).  n: 1..16 for
+   MK_GEN_ER, 2..16 otherwise. */
+int mk_stress_relation(int32_t gen, uint64_t seed, int32_t n, uint64_t s, uint32_t *succ);
+
+/* Relation words: relations are evaluated 32 at a time, bit-sliced.  Block
+   b of a relation list holds relations 32b .. 32b+31; its word (w, v) is
+   d_words[(b * n + w) * n + v], whose bit l is R(w, v) of relation 32b + l
+   (zero past the end of the list).  mk_relation_words gives the number of
+   uint32 words for `count` relations. */
+uint64_t mk_relation_words(int32_t n, uint64_t count);
+
+/* Generate relations first .. first+count-1 of generator gen on the device:
+   their words into d_words (may be NULL) and their successor masks into
+   d_succ[i * 16 + w] (may be NULL; rows w >= n are zero). */
+int mk_generate_relations(int32_t gen, uint64_t seed, int32_t n, uint64_t first, uint64_t count,
+                          uint32_t *d_words, uint32_t *d_succ, void *stream);
+
+/* Pack a caller's relation list (d_succ[i * 16 + w], i < count) into words. */
+int mk_pack_relations(const uint32_t *d_succ, int32_t n, uint64_t count, uint32_t *d_words,
+                      void *stream);
+
+typedef struct {
+    int32_t n;             /* worlds of every relation, 1..16                */
+    int32_t count_splits;  /* 1: also count, per pair, the relations that   */
+                           /* split it (d_nsplit); 0: first split only, and  */
+                           /* a pair whose key already lies below every key  */
+                           /* a CTA could produce is skipped by that CTA     */
+    uint64_t count;        /* relations in d_words                           */
+    uint64_t index_base;   /* relation index of the list's first relation    */
+    mk_tune tune;          /* tile: pairs per CTA, 1..64 (0 = 16)            */
+} mk_stress_cfg;
+
+/* Separation over a relation list (Def. 2, Prop. 4 on explicit frames): for
+   each pair i, the least (relation, valuation, world) at which phi_i and
+   psi_i differ, relations in list order, valuations exhaustive
+   (x = 0 .. 2^(k n)-1, which requires k*n <= 16; a pair beyond that sets
+   MK_ST_LIMIT and is skipped), merged into d_key[i] by atomic minimum as
+       (index_base + position) << 20 | x << 4 | w
+   (d_key must hold UINT64_MAX or an earlier call's key; positions < 2^44).
+   With count_splits, d_nsplit[i] (cleared by the caller) is increased by the
+   number of relations on which the pair differs for some valuation. */
+int mk_stress_separate(const mk_program *d_phi, const mk_program *d_psi, int32_t npairs,
+                       const uint32_t *d_words, const mk_stress_cfg *cfg, uint64_t *d_key,
+                       uint32_t *d_nsplit, int32_t *d_status, void *stream);
+
 /* ------------------------------------------------------------- misc */
 const char *mk_strerror(int code);
 int mk_status_error(int32_t status);   /* MK_OK or the MK_E_* for status bits */

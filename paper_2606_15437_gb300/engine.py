@@ -617,6 +617,240 @@ def proposal_experiment(n_formulas=10000, universe=5_467_766, k=1024, train_iden
 
 # ------------------------------------------------------------ sharding
 
+# ------------------------------------------------------------ large frames
+class RelationSet:
+    """Relations on n <= 16 worlds in device memory, bit-sliced 32 to a
+    block: drawn by an adversarial generator on the device
+    (mk_generate_relations) or packed from explicit successor masks
+    (mk_pack_relations), e.g. the stress templates."""
+
+    def __init__(self, n, count, d_words, succ_host=None, gen=None, seed=0, first=0):
+        self.n, self.count, self.d_words = int(n), int(count), d_words
+        self.succ_host, self.gen, self.seed, self.first = succ_host, gen, seed, first
+
+    @classmethod
+    def generated(cls, gen, seed, n, first, count, device="cuda", stream=None):
+        words = torch.empty(max(1, mk.relation_words(n, count)), dtype=torch.int32, device=device)
+        mk.generate_relations_raw(gen, seed, n, first, count, words.data_ptr(), 0, _stream_ptr(stream))
+        return cls(n, count, words, gen=mk.gen_index(gen), seed=seed, first=first)
+
+    @classmethod
+    def from_succ(cls, succ, n, device="cuda", stream=None):
+        a = np.zeros((len(succ), 16), np.uint32)
+        for i, row in enumerate(succ):
+            a[i, :len(row)] = row
+        d = torch.from_numpy(a.view(np.int32)).to(device)
+        words = torch.empty(max(1, mk.relation_words(n, len(a))), dtype=torch.int32, device=device)
+        mk.pack_relations_raw(d.data_ptr(), n, len(a), words.data_ptr(), _stream_ptr(stream))
+        obj = cls(n, len(a), words, succ_host=a)
+        obj._keep = d
+        return obj
+
+    @classmethod
+    def templates(cls, n, device="cuda"):
+        return cls.from_succ([mk.template(t, n) for t in range(mk.NUM_TEMPLATES)], n, device)
+
+    def relation(self, i):
+        """Successor masks of relation i (host)."""
+        if self.succ_host is not None:
+            return [int(x) for x in self.succ_host[i, :self.n]]
+        return mk.stress_relation(self.gen, self.seed, self.n, self.first + i)
+
+
+class StressJob:
+    """Separation of (phi, psi) pairs over relation lists on up to 16
+    worlds (mk_stress_separate)."""
+
+    def __init__(self, pairs, device="cuda"):
+        if not torch.cuda.is_available():
+            raise RuntimeError("StressJob needs a CUDA device (there is no CPU fallback)")
+        self.pairs = list(pairs)
+        self.npairs = len(self.pairs)
+        self.device = torch.device(device)
+        self.pa = mk.compile_batch([a for a, _ in self.pairs])
+        self.pb = mk.compile_batch([b for _, b in self.pairs])
+        self.k = np.maximum(self.pa["nvars"], self.pb["nvars"]).astype(np.int64)
+        self.d_pa = _dev_bytes(self.pa, self.device).view(self.npairs, -1)
+        self.d_pb = _dev_bytes(self.pb, self.device).view(self.npairs, -1)
+        self.d_status = torch.zeros(1, dtype=torch.int32, device=self.device)
+
+    def eligible(self, n):
+        """Pairs whose valuations at n worlds are exhaustive within the
+        kernel's limit (k*n <= 16)."""
+        return np.nonzero(self.k * n <= 16)[0]
+
+    def launch(self, rels, idx=None, count_splits=False, tile=0, d_key=None, d_cnt=None, stream=None):
+        """Launch on the pairs idx (default: all); returns the device key and
+        count tensors (keys merged by minimum into d_key if given)."""
+        idx = np.arange(self.npairs) if idx is None else np.asarray(idx)
+        sel = torch.from_numpy(idx.astype(np.int64)).to(self.device)
+        pa = self.d_pa.index_select(0, sel).contiguous()
+        pb = self.d_pb.index_select(0, sel).contiguous()
+        if d_key is None:
+            d_key = torch.full((len(idx),), -1, dtype=torch.int64, device=self.device)
+        if count_splits and d_cnt is None:
+            d_cnt = torch.zeros(len(idx), dtype=torch.int32, device=self.device)
+        cfg = mk.stress_cfg(rels.n, rels.count, 0, count_splits, tile)
+        mk.stress_separate_raw(pa.data_ptr(), pb.data_ptr(), len(idx), rels.d_words.data_ptr(), cfg,
+                               d_key.data_ptr(), d_cnt.data_ptr() if count_splits else 0,
+                               self.d_status.data_ptr(), _stream_ptr(stream))
+        self._keep = (pa, pb)
+        return d_key, d_cnt
+
+    def check_status(self):
+        st = int(self.d_status.item())
+        if st:
+            raise mk.MkError(mk.status_error(st), "device status 0x%x" % st)
+
+    def run(self, rels, idx=None, count_splits=False, tile=0):
+        """First split keys (np.uint64) and, with count_splits, the number
+        of relations splitting each pair."""
+        self.d_status.zero_()
+        d_key, d_cnt = self.launch(rels, idx, count_splits, tile)
+        torch.cuda.synchronize(self.device)
+        self.check_status()
+        keys = d_key.cpu().numpy().view(np.uint64)
+        return keys, (d_cnt.cpu().numpy().astype(np.int64) if count_splits else None)
+
+    def certify(self, i, key, rels):
+        """mk_certify on the split that key names for pair i."""
+        s, x, w = mk.decode_stress_key(key)
+        n = rels.n
+        full = (1 << n) - 1
+        val = [(x >> (v * n)) & full for v in range(int(self.k[i]))]
+        a, b = self.pairs[i]
+        return mk.certify(a, n, rels.relation(s), val, w, psi=b) == 1
+
+    def evals(self, idx, n, relations):
+        """Pair evaluations (relation x valuation) of a full scan."""
+        return float(sum(relations * (1 << (int(self.k[i]) * n)) for i in idx))
+
+    def lop3(self, idx, n, relations):
+        """Algorithmic logic ops of a full scan (both programs and the
+        difference test, per 32 relations)."""
+        tot = 0.0
+        for i in idx:
+            per = lop3_per_eval(self.pa[i], n) + lop3_per_eval(self.pb[i], n)
+            tot += per * relations * (1 << (int(self.k[i]) * n))
+        return tot
+
+
+def template_similarity(succ, n):
+    """Largest Jaccard similarity (shared edges over edges of either) of a
+    relation to the 39 stress templates of the same size; 1 for a template
+    itself.  A witness below 0.5 counts as non-template."""
+    def es(rows):
+        return {(w, v) for w in range(n) for v in range(n) if (rows[w] >> v) & 1}
+    e = es(succ)
+    best = 0.0
+    for t in range(mk.NUM_TEMPLATES):
+        te = es(mk.template(t, n))
+        u = len(e | te)
+        best = max(best, (len(e & te) / u) if u else 1.0)
+    return best
+
+
+def template_stress(pairs, sizes=range(6, 17), job=None, device="cuda"):
+    """Challenge pairs on the 39 templates at every size (Sec. 7 mining):
+    for each pair the first (n, template, valuation, world) at which it
+    splits, sizes ascending, or None.  Pairs with k*n > 16 skip size n."""
+    job = job or StressJob(pairs, device)
+    first = [None] * job.npairs
+    for n in sizes:
+        todo = [i for i in job.eligible(n) if first[i] is None]
+        if not todo:
+            continue
+        rels = RelationSet.templates(n, device)
+        keys, _ = job.run(rels, todo)
+        for i, key in zip(todo, keys):
+            d = mk.decode_stress_key(int(key))
+            if d is not None:
+                assert job.certify(i, int(key), rels)
+                first[i] = (n,) + d
+    return first
+
+
+def mine_context_words(max_nodes=21, sizes=range(6, 17), device="cuda", log=None):
+    """Automated context-word mining (Sec. 7): every candidate
+    (C^m b, C^(m+1) b) is scanned on every K frame through five worlds; a is
+    the largest size through which the pair agrees (exact prefix); pairs
+    with a = 5 are stressed on the templates at 6..16 worlds.  Score
+    J = a + 2 [template witness after a] - 0.02 (|phi| + |psi|) + 0.1/|C|.
+    Returns rows sorted by J (highest first)."""
+    cands = workloads.mining_candidates(max_nodes)
+    pairs = [(a, b) for a, b, _ in cands]
+    sj = SeparateJob(pairs, 1, 5, device=device)
+    keys = sj.run()
+    rows = []
+    for i, (a, b, cl) in enumerate(cands):
+        key = int(keys[i])
+        ag = 5 if key == mk.NO_KEY else mk.split_n(key) - 1
+        rows.append({"phi": a, "psi": b, "word": cl, "a": ag, "nodes": workloads.nodes(a) + workloads.nodes(b),
+                     "prefix_key": key, "template": None})
+    surv = [i for i, r in enumerate(rows) if r["a"] == 5]
+    if log:
+        log("mining: %d candidates, %d agree through five worlds" % (len(rows), len(surv)))
+    if surv:
+        tw = template_stress([pairs[i] for i in surv], sizes, device=device)
+        for i, t in zip(surv, tw):
+            rows[i]["template"] = t
+    for r in rows:
+        late = r["template"] is not None and r["template"][0] > r["a"]
+        r["J"] = r["a"] + 2.0 * late - 0.02 * r["nodes"] + 0.1 / r["word"]
+    rows.sort(key=lambda r: (-r["J"], r["phi"]))
+    return rows
+
+
+def adversarial_search(pairs, generators=mk.GENERATORS, sizes=(6, 8, 10, 12, 14, 16), relations=1 << 18,
+                       seed=6, k_max=lambda n: 1 if n <= 12 else 0, device="cuda", log=None):
+    """Adversarial frame synthesis (Table 2): for every generator and size,
+    `relations` relations are drawn on the device and every eligible pair
+    (k <= k_max(n): one-variable pairs through 12 worlds, constant pairs
+    beyond) is scanned on all of them.  Per panel: relations, pair-relation
+    tests, valuation evaluations, pairs split (each first split certified by
+    mk_certify), non-template witnesses, GPU seconds (CUDA events)."""
+    job = StressJob(pairs, device)
+    rows, first = [], [None] * job.npairs
+    for gen in generators:
+        for n in sizes:
+            idx = np.array([i for i in job.eligible(n) if job.k[i] <= k_max(n)], np.int64)
+            if len(idx) == 0:
+                continue
+            rels = RelationSet.generated(gen, seed, n, 0, relations, device)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            job.d_status.zero_()
+            ev0.record()
+            d_key, d_cnt = job.launch(rels, idx, count_splits=True)
+            ev1.record()
+            torch.cuda.synchronize()
+            job.check_status()
+            keys = d_key.cpu().numpy().view(np.uint64)
+            cnt = d_cnt.cpu().numpy()
+            hits = cert = nontpl = 0
+            for j, i in enumerate(idx):
+                key = int(keys[j])
+                if key == mk.NO_KEY:
+                    continue
+                hits += 1
+                ok = job.certify(int(i), key, rels)
+                cert += ok
+                s, _, _ = mk.decode_stress_key(key)
+                sim = template_similarity(rels.relation(s), n)
+                nontpl += sim < 0.5
+                if first[i] is None or (n, gen) < first[i][:2]:
+                    first[i] = (n, gen, s, sim)
+            row = {"generator": gen, "n": n, "relations": relations, "pairs": len(idx),
+                   "tests": len(idx) * relations, "evals": job.evals(idx, n, relations),
+                   "lop3": job.lop3(idx, n, relations), "split_pairs": hits, "certified": cert,
+                   "non_template": nontpl, "split_relations": int(cnt.sum()),
+                   "gpu_s": ev0.elapsed_time(ev1) / 1e3}
+            rows.append(row)
+            if log:
+                log("  %-8s n=%2d pairs=%4d split=%4d cert=%4d non-template=%4d  %.3f s" %
+                    (gen, n, len(idx), hits, cert, nontpl, row["gpu_s"]))
+    return rows, first
+
+
 def shard_range(total, rank, world):
     """[lo, hi) of the rank-th of ``world`` near-equal contiguous shards of
     [0, total) (frame K indices for the census, pairs for separation)."""

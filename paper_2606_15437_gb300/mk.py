@@ -91,6 +91,11 @@ assert PROGRAM_DTYPE.itemsize == ctypes.sizeof(mk_program) == 104
 _lib = None
 _lock = threading.Lock()
 
+class mk_stress_cfg(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("count_splits", ctypes.c_int32), ("count", ctypes.c_uint64),
+                ("index_base", ctypes.c_uint64), ("tune", mk_tune)]
+
+
 _SIGS = {
     "mk_compile": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(mk_program), ctypes.POINTER(ctypes.c_int32)]),
     "mk_compile_iff": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(mk_program),
@@ -149,6 +154,17 @@ _SIGS = {
     "mk_mlp_infer_bf16": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "mk_template": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
+    "mk_stress_relation": (ctypes.c_int, [ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint64,
+                                          ctypes.c_void_p]),
+    "mk_relation_words": (ctypes.c_uint64, [ctypes.c_int32, ctypes.c_uint64]),
+    "mk_generate_relations": (ctypes.c_int, [ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint64,
+                                             ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "mk_pack_relations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
+    "mk_stress_separate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                          ctypes.POINTER(mk_stress_cfg), ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
     "mk_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mk_status_error": (ctypes.c_int, [ctypes.c_int32]),
     "mk_version": (ctypes.c_int, []),
@@ -470,3 +486,60 @@ def mlp_infer_workspace_size(batch, features, hidden):
 def mlp_infer_bf16_raw(d_params, features, hidden, d_vec, d_pa, d_pb, batch, d_logits, d_ws, ws_bytes, stream):
     _check(lib().mk_mlp_infer_bf16(d_params, features, hidden, d_vec, d_pa, d_pb, batch, d_logits, d_ws, ws_bytes,
                                    stream), "mk_mlp_infer_bf16")
+
+
+# ------------------------------------------------------------ large frames
+NUM_TEMPLATES = 39
+GENERATORS = ("er", "flip", "scc", "deadend", "backedge", "permscc")
+
+
+def gen_index(gen):
+    return GENERATORS.index(gen) if isinstance(gen, str) else int(gen)
+
+
+def template(tid, n):
+    """Successor masks of stress template ``tid`` on n worlds (host)."""
+    out = (ctypes.c_uint32 * 16)()
+    _check(lib().mk_template(int(tid), int(n), out), "mk_template")
+    return [int(out[w]) for w in range(n)]
+
+
+def stress_relation(gen, seed, n, s):
+    """Successor masks of relation ``s`` of generator ``gen`` (host)."""
+    out = (ctypes.c_uint32 * 16)()
+    _check(lib().mk_stress_relation(gen_index(gen), int(seed), int(n), int(s), out), "mk_stress_relation")
+    return [int(out[w]) for w in range(n)]
+
+
+def relation_words(n, count):
+    return int(lib().mk_relation_words(int(n), int(count)))
+
+
+def generate_relations_raw(gen, seed, n, first, count, d_words, d_succ, stream):
+    _check(lib().mk_generate_relations(gen_index(gen), int(seed), int(n), int(first), int(count), d_words,
+                                       d_succ, stream), "mk_generate_relations")
+
+
+def pack_relations_raw(d_succ, n, count, d_words, stream):
+    _check(lib().mk_pack_relations(d_succ, int(n), int(count), d_words, stream), "mk_pack_relations")
+
+
+def stress_cfg(n, count, index_base=0, count_splits=False, tile=0):
+    c = mk_stress_cfg()
+    c.n, c.count, c.index_base, c.count_splits = int(n), int(count), int(index_base), int(bool(count_splits))
+    c.tune.tile = int(tile)
+    return c
+
+
+def stress_separate_raw(d_phi, d_psi, npairs, d_words, cfg, d_key, d_nsplit, d_status, stream):
+    _check(lib().mk_stress_separate(d_phi, d_psi, int(npairs), d_words, ctypes.byref(cfg), d_key, d_nsplit,
+                                    d_status, stream), "mk_stress_separate")
+
+
+def decode_stress_key(key):
+    """(relation index, valuation, world) of a key mk_stress_separate wrote,
+    None for no split."""
+    key = int(key)
+    if key == NO_KEY:
+        return None
+    return key >> 20, (key >> 4) & 0xFFFF, key & 15

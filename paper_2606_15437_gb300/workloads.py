@@ -270,6 +270,31 @@ def context_word_formulas(max_nodes=21, max_depth=10):
     return out
 
 
+MINING_BASES = ("T", "F", "p", "(p->p)", "(p&~p)", "(~p|p)")
+
+
+def mining_candidates(max_nodes=21):
+    """Context-word mining candidates of Sec. 7: for every context word C
+    over {[], <>} of length 1-3, every base b in {T, F, p, p->p, p&~p,
+    ~p|p} and every m >= 1 with |C^(m+1) b| <= max_nodes, the pair
+    (C^m b, C^(m+1) b).  Returns (phi, psi, word_length) triples in a fixed
+    order (words by length, then text; bases in the order above; m up)."""
+    words = [""]
+    for _ in range(3):
+        words = [w + c for w in words for c in ("[]", "<>")] + words
+    words = sorted({w for w in words if w}, key=lambda w: (len(w), w))
+    out = []
+    for C in words:
+        cl = len(C) // 2
+        for b in MINING_BASES:
+            bn = nodes(b)
+            m = 1
+            while cl * (m + 1) + bn <= max_nodes:
+                out.append((C * m + b, C * (m + 1) + b, cl))
+                m += 1
+    return out
+
+
 def proposal_formulas(seed=5, count=10000, bases=2000):
     """Retrieval corpus, like the paper's corpus of representatives of
     sizes 1-21 and modal depths 0-10, most with a Boolean connective (Sec. 9):
