@@ -57,7 +57,8 @@ def parse():
                     help="census5:F -- run the K n=5 layer of the first F five-world formulas twice "
                          "(a warm-up and the launch an ncu capture selects with -s 1 -c 1), then exit; "
                          "separation:P -- the same for the first P separation pairs at n=6; "
-                         "stress:P -- the first P mining candidates on 2^16 16-world relations")
+                         "stress:P -- the first P mining candidates on 2^13 12-world relations (two "
+                         "stress_kernel launches per run: constant pairs, then pairs with a variable)")
     ap.add_argument("--relations", type=int, default=1 << 18,
                     help="relations per generator and size (--workload adversarial)")
     ap.add_argument("--workload", default="census5", choices=["census5", "uneven", "separation", "learned", "adversarial"],
@@ -569,12 +570,13 @@ def run_profile_case(spec):
     elif kind == "separation":
         job = E.SeparateJob(W.separation_pairs(4)[:count], 6, 6, frame_lo=0, frame_hi=1 << 30)
     elif kind == "stress":
+        # the adversarial panels' dominant shape: one-variable and constant
+        # pairs on 12-world Erdos-Renyi relations, every relation and valuation
         pairs = [(a, b) for a, b, _ in W.mining_candidates()[:count]]
         sj = E.StressJob(pairs)
-        rels = E.RelationSet.generated("er", 6, 16, 0, 1 << 16)
-        idx = np.nonzero(sj.k == 0)[0]          # constant pairs: one valuation per relation
-        sj.run(rels, idx, count_splits=True)
-        sj.run(rels, idx, count_splits=True)
+        rels = E.RelationSet.generated("er", 6, 12, 0, 1 << 13)
+        sj.run(rels, count_splits=True)
+        sj.run(rels, count_splits=True)
         torch.cuda.synchronize()
         print("profile case %s done" % spec)
         return

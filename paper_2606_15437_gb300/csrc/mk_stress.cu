@@ -52,8 +52,15 @@ struct WS {
     static constexpr int XW = (31 / N + 1) * RN;    // exchange words per warp and unit (idle lanes too)
 };
 
+// Units per dispatched instruction: UB relation blocks x V valuations.
+// Constant pairs have one valuation, so their launch walks UB0 blocks;
+// pairs with variables walk UB1 blocks under V consecutive valuations each
+// (the edge registers of a block serve all V valuations).
 template <int N>
-constexpr int st_units() { return N <= 5 ? 8 : N <= 8 ? 6 : 4; }
+constexpr int st_ub0() { return N <= 5 ? 8 : N <= 8 ? 6 : 4; }
+template <int N>
+constexpr int st_ub1() { return 1; }
+constexpr int ST_V = 16;
 
 struct StressArgs {
     const mk_program *phi;
@@ -66,6 +73,7 @@ struct StressArgs {
     uint64_t blk_lo;         // first relation block of this launch
     uint64_t index_base;
     uint32_t vchunk;         // valuations per grid.z slice
+    int32_t with_vars;       // 0: this launch takes the constant pairs, 1: the others
     int32_t count_splits;
     uint64_t *key;
     uint32_t *nsplit;
@@ -97,12 +105,13 @@ __device__ __forceinline__ void decode_ws(const mk_program &p, uint8_t *ops, uin
     offs[p.n_instr] = 0;
 }
 
-// One modal step for all U units: publish this world's word, read the
-// group's n words, combine with this world's edge row.
-template <int N, int U, bool BOX>
-__device__ __forceinline__ void modal_ws(uint32_t (&A)[U], const uint32_t (&E)[U][N], uint32_t *xw, int xo, int j,
-                                         bool active) {
-    constexpr int RN = WS<N>::RN, XW = WS<N>::XW;
+// One modal step for all U = UB*V units (unit u: block u/V): publish this
+// world's word, read the group's n words, combine with this world's edge
+// row of the unit's block.
+template <int N, int UB, int V, bool BOX>
+__device__ __forceinline__ void modal_ws(uint32_t (&A)[UB * V], const uint32_t (&E)[UB][N], uint32_t *xw, int xo,
+                                         int j, bool active) {
+    constexpr int RN = WS<N>::RN, XW = WS<N>::XW, U = UB * V;
 #pragma unroll
     for (int u = 0; u < U; ++u)
         if (active) xw[u * XW + xo + j] = A[u];
@@ -122,32 +131,34 @@ __device__ __forceinline__ void modal_ws(uint32_t (&A)[U], const uint32_t (&E)[U
         uint32_t acc = BOX ? 0xFFFFFFFFu : 0u;
 #pragma unroll
         for (int v = 0; v < N; ++v) {
-            if (BOX) acc &= t[v] | ~E[u][v];
-            else acc |= t[v] & E[u][v];
+            if (BOX) acc &= t[v] | ~E[u / V][v];
+            else acc |= t[v] & E[u / V][v];
         }
         A[u] = acc;
     }
     __syncwarp();
 }
 
-// Run a decoded program on this thread's world of U relation blocks under
-// valuation x (xj = x >> j).  Every thread of a warp runs the same program,
-// so the __syncwarp of the modal steps is reached by all 32 lanes.
-template <int N, int U, int BLOCK>
-__device__ __forceinline__ void run_ws(const uint8_t *ops, const uint16_t *offs, uint32_t xj,
-                                       const uint32_t (&E)[U][N], uint32_t *stack, uint32_t *xw, int xo, int j,
-                                       bool active, uint32_t (&A)[U]) {
+// Run a decoded program on this thread's world of U = UB*V units, unit u
+// being block u/V under valuation x + u%V (xj[v] = (x + v) >> j).  Every
+// thread of a warp runs the same program, so the __syncwarp of the modal
+// steps is reached by all 32 lanes.
+template <int N, int UB, int V, int BLOCK>
+__device__ __forceinline__ void run_ws(const uint8_t *ops, const uint16_t *offs, const uint32_t (&xj)[V],
+                                       const uint32_t (&E)[UB][N], uint32_t *stack, uint32_t *xw, int xo, int j,
+                                       bool active, uint32_t (&A)[UB * V]) {
+    constexpr int U = UB * V;
     uint32_t op = ops[0], off = offs[0];
     for (int pc = 1;; ++pc) {
         const uint32_t op_next = ops[pc], off_next = offs[pc];
         uint32_t *st = stack + off;
-        // atom truth word of p_i at this world: only variable operands
-        // (off = i*N < 16) are shifts; stack operands never reach it
-#define MK_ATOM (0u - ((xj >> off) & 1u))
+        // atom truth word of p_i at this world under unit u's valuation:
+        // only variable operands (off = i*N < 16) are shifts
+#define MK_ATOM(u) (0u - ((xj[(u) % V] >> off) & 1u))
         switch (op) {
         case MK_OP_LDV:
 #pragma unroll
-            for (int u = 0; u < U; ++u) A[u] = MK_ATOM;
+            for (int u = 0; u < U; ++u) A[u] = MK_ATOM(u);
             break;
         case MK_OP_LDT:
 #pragma unroll
@@ -162,10 +173,10 @@ __device__ __forceinline__ void run_ws(const uint8_t *ops, const uint16_t *offs,
             for (int u = 0; u < U; ++u) A[u] = ~A[u];
             break;
         case MK_OP_BOX:
-            modal_ws<N, U, true>(A, E, xw, xo, j, active);
+            modal_ws<N, UB, V, true>(A, E, xw, xo, j, active);
             break;
         case MK_OP_DIA:
-            modal_ws<N, U, false>(A, E, xw, xo, j, active);
+            modal_ws<N, UB, V, false>(A, E, xw, xo, j, active);
             break;
         case MK_OP_PUSH:
 #pragma unroll
@@ -193,19 +204,19 @@ __device__ __forceinline__ void run_ws(const uint8_t *ops, const uint16_t *offs,
             break;
         case MK_OP_AND_V:
 #pragma unroll
-            for (int u = 0; u < U; ++u) A[u] &= MK_ATOM;
+            for (int u = 0; u < U; ++u) A[u] &= MK_ATOM(u);
             break;
         case MK_OP_OR_V:
 #pragma unroll
-            for (int u = 0; u < U; ++u) A[u] |= MK_ATOM;
+            for (int u = 0; u < U; ++u) A[u] |= MK_ATOM(u);
             break;
         case MK_OP_IMP_V:
 #pragma unroll
-            for (int u = 0; u < U; ++u) A[u] = ~A[u] | MK_ATOM;
+            for (int u = 0; u < U; ++u) A[u] = ~A[u] | MK_ATOM(u);
             break;
         case MK_OP_RIMP_V:
 #pragma unroll
-            for (int u = 0; u < U; ++u) A[u] = ~MK_ATOM | A[u];
+            for (int u = 0; u < U; ++u) A[u] = ~MK_ATOM(u) | A[u];
             break;
         case MK_OP_END:
             return;
@@ -218,8 +229,9 @@ __device__ __forceinline__ void run_ws(const uint8_t *ops, const uint16_t *offs,
 #undef MK_ATOM
 }
 
-template <int N, int U, int BLOCK>
+template <int N, int UB, int V, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 2) stress_kernel(StressArgs a) {
+    constexpr int U = UB * V;
     using SM = StressSmem<N, U, BLOCK>;
     using L = WS<N>;
     constexpr int GROUPS = (BLOCK / 32) * L::GW;
@@ -242,7 +254,7 @@ __global__ void __launch_bounds__(BLOCK, 2) stress_kernel(StressArgs a) {
     const int g = lane / N, j = lane - g * N;
     const bool active = g < L::GW;
     const int G = wi * L::GW + (active ? g : 0);
-    const uint64_t cta_b0 = a.blk_lo + (uint64_t)blockIdx.x * GROUPS * U;
+    const uint64_t cta_b0 = a.blk_lo + (uint64_t)blockIdx.x * GROUPS * UB;
     const uint32_t x_lo = blockIdx.z * a.vchunk;
     const unsigned long long floor_key = (a.index_base + (cta_b0 << 5)) << ST_KEY_S;
 
@@ -252,15 +264,16 @@ __global__ void __launch_bounds__(BLOCK, 2) stress_kernel(StressArgs a) {
     const int np = min(tile, a.npairs - p0);
     for (int i = tid; i < np; i += BLOCK) {
         const mk_program &pa = a.phi[p0 + i], &pb = a.psi[p0 + i];
-        const bool first_cta = blockIdx.x == 0 && blockIdx.z == 0;
+        const bool first_cta = blockIdx.x == 0 && blockIdx.z == 0 && a.blk_lo == 0;
         int ok = program_ok(pa) && program_ok(pb);
-        if (!ok && first_cta) atomicOr(a.status, (int)MK_ST_PROGRAM);
+        if (!ok && first_cta && !a.with_vars) atomicOr(a.status, (int)MK_ST_PROGRAM);
         const int k = pa.nvars > pb.nvars ? pa.nvars : pb.nvars;
+        if (ok && (k > 0) != (a.with_vars != 0)) ok = 0;       // the other launch's pair
         if (ok && k * N > 16) {
             ok = 0;
             if (first_cta) atomicOr(a.status, (int)MK_ST_LIMIT);
         }
-        if (ok && x_lo >= (1u << (k * N))) ok = 0;     // nothing in this valuation slice
+        if (ok && x_lo >= (1u << (k * N))) ok = 0;             // nothing in this valuation slice
         if (ok && !a.count_splits && ((volatile unsigned long long *)a.key)[p0 + i] < floor_key) ok = 0;
         s_na[i] = ok ? pa.n_instr : -1;
         s_nb[i] = pb.n_instr;
@@ -276,22 +289,22 @@ __global__ void __launch_bounds__(BLOCK, 2) stress_kernel(StressArgs a) {
     __syncthreads();
     if (s_active == 0) return;
 
-    // this thread's rows of its U relation blocks
-    uint32_t E[U][N];
-    uint32_t valid[U];
+    // this thread's rows of its UB relation blocks
+    uint32_t E[UB][N];
+    uint32_t valid[UB];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const uint64_t b = cta_b0 + (uint64_t)G * U + u;
-        valid[u] = 0;
-        if (active && b < a.nblocks) {
-            const uint32_t *row = a.words + (b * N + j) * N;
+    for (int b = 0; b < UB; ++b) {
+        const uint64_t blk = cta_b0 + (uint64_t)G * UB + b;
+        valid[b] = 0;
+        if (active && blk < a.nblocks) {
+            const uint32_t *row = a.words + (blk * N + j) * N;
 #pragma unroll
-            for (int v = 0; v < N; ++v) E[u][v] = row[v];
-            const uint64_t left = a.count - (b << 5);
-            valid[u] = left >= 32 ? 0xFFFFFFFFu : ((1u << left) - 1u);
+            for (int v = 0; v < N; ++v) E[b][v] = row[v];
+            const uint64_t left = a.count - (blk << 5);
+            valid[b] = left >= 32 ? 0xFFFFFFFFu : ((1u << left) - 1u);
         } else {
 #pragma unroll
-            for (int v = 0; v < N; ++v) E[u][v] = 0u;
+            for (int v = 0; v < N; ++v) E[b][v] = 0u;
         }
     }
     uint32_t *xw = s_xbuf + (size_t)wi * U * L::XW;
@@ -304,31 +317,34 @@ __global__ void __launch_bounds__(BLOCK, 2) stress_kernel(StressArgs a) {
         const uint32_t x_hi = min(nval, x_lo + a.vchunk);
         const uint8_t *oa = s_ops_a + fi * ST_OPS_STRIDE, *ob = s_ops_b + fi * ST_OPS_STRIDE;
         const uint16_t *fa = s_offs_a + fi * ST_OPS_STRIDE, *fb = s_offs_b + fi * ST_OPS_STRIDE;
-        int best_o = U * 32;
+        int best_o = UB * 32;
         uint32_t best_x = 0;
-        uint32_t hm[U];
+        uint32_t hm[UB];
 #pragma unroll
-        for (int u = 0; u < U; ++u) hm[u] = 0;
-        for (uint32_t x = x_lo; x < x_hi; ++x) {
-            uint32_t A[U], B[U];
-            const uint32_t xj = x >> j;
-            run_ws<N, U, BLOCK>(oa, fa, xj, E, stk, xw, xo, j, active, A);
-            run_ws<N, U, BLOCK>(ob, fb, xj, E, stk, xw, xo, j, active, B);
+        for (int b = 0; b < UB; ++b) hm[b] = 0;
+        for (uint32_t x = x_lo; x < x_hi; x += V) {
+            uint32_t A[U], B[U], xj[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) xj[v] = (x + v) >> j;
+            run_ws<N, UB, V, BLOCK>(oa, fa, xj, E, stk, xw, xo, j, active, A);
+            run_ws<N, UB, V, BLOCK>(ob, fb, xj, E, stk, xw, xo, j, active, B);
+            // blocks outer, valuations inner: for one relation the first
+            // unit with a difference has the least valuation
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const uint32_t d = (A[u] ^ B[u]) & valid[u];
-                hm[u] |= d;
+                const uint32_t d = (x + (u % V) < x_hi) ? (A[u] ^ B[u]) & valid[u / V] : 0u;
+                hm[u / V] |= d;
                 if (d) {
-                    const int o = u * 32 + __ffs(d) - 1;
+                    const int o = (u / V) * 32 + __ffs(d) - 1;
                     if (o < best_o) {
                         best_o = o;
-                        best_x = x;
+                        best_x = x + (u % V);
                     }
                 }
             }
         }
-        if (active && best_o < U * 32) {
-            const uint64_t s = a.index_base + ((cta_b0 + (uint64_t)G * U + (uint64_t)(best_o >> 5)) << 5) +
+        if (active && best_o < UB * 32) {
+            const uint64_t s = a.index_base + ((cta_b0 + (uint64_t)G * UB + (uint64_t)(best_o >> 5)) << 5) +
                                (uint64_t)(best_o & 31);
             const unsigned long long key = (s << ST_KEY_S) | ((uint64_t)best_x << ST_KEY_X) | (uint64_t)j;
             atomicMin(&s_key[fi], key);
@@ -336,16 +352,16 @@ __global__ void __launch_bounds__(BLOCK, 2) stress_kernel(StressArgs a) {
         if (a.count_splits) {
             // relations of the group split at any of its worlds
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (active) xw[u * L::XW + xo + j] = hm[u];
+            for (int b = 0; b < UB; ++b)
+                if (active) xw[b * L::XW + xo + j] = hm[b];
             __syncwarp();
             if (active && j == 0) {
                 uint32_t c = 0;
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
+                for (int b = 0; b < UB; ++b) {
                     uint32_t m = 0;
 #pragma unroll
-                    for (int v = 0; v < N; ++v) m |= xw[u * L::XW + xo + v];
+                    for (int v = 0; v < N; ++v) m |= xw[b * L::XW + xo + v];
                     c += __popc(m);
                 }
                 if (c) atomicAdd(&s_cnt[fi], c);
@@ -408,14 +424,13 @@ void st_smem(K kern, size_t bytes) {
     g_st_attr.push_back((const void *)kern);
 }
 
-template <int N>
-void launch_stress(StressArgs a, uint64_t blk_hi, uint32_t vz, cudaStream_t s) {
-    constexpr int U = st_units<N>();
+template <int N, int UB, int V>
+void launch_stress_kind(StressArgs a, uint64_t blk_hi, uint32_t vz, cudaStream_t s) {
     constexpr int GROUPS = (ST_BLOCK / 32) * WS<N>::GW;
-    using SM = StressSmem<N, U, ST_BLOCK>;
-    auto kern = stress_kernel<N, U, ST_BLOCK>;
+    using SM = StressSmem<N, UB * V, ST_BLOCK>;
+    auto kern = stress_kernel<N, UB, V, ST_BLOCK>;
     st_smem(kern, SM::total(ST_MAX_TILE));
-    const uint64_t per_cta = (uint64_t)GROUPS * U;
+    const uint64_t per_cta = (uint64_t)GROUPS * UB;
     // ascending launches of at most 4096 CTAs: pairs split in one launch are
     // skipped by the later ones (first-split mode)
     const uint64_t chunk = per_cta * 4096;
@@ -426,6 +441,19 @@ void launch_stress(StressArgs a, uint64_t blk_hi, uint32_t vz, cudaStream_t s) {
         dim3 grid((unsigned)((hi - lo + per_cta - 1) / per_cta), (unsigned)((a.npairs + a.tile - 1) / a.tile), vz);
         kern<<<grid, ST_BLOCK, SM::total(a.tile), s>>>(c);
     }
+}
+
+// Two launches over the pair list: constant pairs (one valuation) and the
+// pairs with variables, each taking only its own pairs.
+template <int N>
+void launch_stress(StressArgs a, uint64_t blk_hi, uint32_t vz, cudaStream_t s) {
+    StressArgs c0 = a;
+    c0.with_vars = 0;
+    c0.vchunk = 1;
+    launch_stress_kind<N, st_ub0<N>(), 1>(c0, blk_hi, 1, s);
+    StressArgs c1 = a;
+    c1.with_vars = 1;
+    launch_stress_kind<N, st_ub1<N>(), ST_V>(c1, blk_hi, vz, s);
 }
 
 void launch_stress_n(int n, const StressArgs &a, uint64_t blk_hi, uint32_t vz, cudaStream_t s) {
@@ -450,7 +478,7 @@ void launch_stress_n(int n, const StressArgs &a, uint64_t blk_hi, uint32_t vz, c
 }
 
 template <int N>
-uint64_t per_cta_blocks() { return (uint64_t)(ST_BLOCK / 32) * WS<N>::GW * st_units<N>(); }
+uint64_t per_cta_blocks() { return (uint64_t)(ST_BLOCK / 32) * WS<N>::GW * st_ub1<N>(); }
 
 uint64_t per_cta_n(int n) {
     switch (n) {
@@ -530,11 +558,21 @@ extern "C" int mk_stress_separate(const mk_program *d_phi, const mk_program *d_p
     if (!cfg || npairs < 0 || !d_status) return MK_E_ARG;
     const int n = cfg->n;
     if (n < 1 || n > MK_MAX_WORLDS_STRESS) return MK_E_ARG;
-    const int tile = cfg->tune.tile ? cfg->tune.tile : 16;
-    if (tile < 1 || tile > ST_MAX_TILE || (cfg->tune.block && cfg->tune.block != ST_BLOCK)) return MK_E_ARG;
+    if (cfg->tune.tile > ST_MAX_TILE || (cfg->tune.block && cfg->tune.block != ST_BLOCK)) return MK_E_ARG;
     if (cfg->index_base + cfg->count >= (1ull << 44)) return MK_E_ARG;
     if (npairs == 0 || cfg->count == 0) return MK_OK;
     if (!d_phi || !d_psi || !d_key || !d_words || (cfg->count_splits && !d_nsplit)) return MK_E_ARG;
+
+    const uint64_t nblocks = (cfg->count + 31) / 32;
+    const uint64_t rel_ctas = (nblocks + per_cta_n(n) - 1) / per_cta_n(n);
+    const uint64_t want = 4 * 152;   // CTAs that fill the GPU a few times over
+    // Pairs per CTA: the caller's, or 16 cut down while the relation list
+    // alone gives too few CTAs.
+    int tile = cfg->tune.tile;
+    if (tile == 0) {
+        tile = 16;
+        while (tile > 1 && rel_ctas * (uint64_t)((npairs + tile - 1) / tile) < want) tile /= 2;
+    }
     if ((npairs + tile - 1) / tile > 65535) return MK_E_ARG;
 
     StressArgs a;
@@ -545,20 +583,19 @@ extern "C" int mk_stress_separate(const mk_program *d_phi, const mk_program *d_p
     a.tile = tile;
     a.words = d_words;
     a.count = cfg->count;
-    a.nblocks = (cfg->count + 31) / 32;
+    a.nblocks = nblocks;
     a.blk_lo = 0;
     a.index_base = cfg->index_base;
     a.count_splits = cfg->count_splits ? 1 : 0;
     a.key = d_key;
     a.nsplit = d_nsplit;
     a.status = d_status;
-    // Cut large valuation ranges over grid.z when the relation list alone
-    // gives too few CTAs (counting needs every relation in one slice).
-    const uint64_t base_ctas = (a.nblocks + per_cta_n(n) - 1) / per_cta_n(n) * (uint64_t)((npairs + tile - 1) / tile);
+    // Then cut large valuation ranges over grid.z (first-split mode only:
+    // counting needs every valuation of a relation in one CTA).
+    const uint64_t base_ctas = rel_ctas * (uint64_t)((npairs + tile - 1) / tile);
     uint32_t vz = 1;
     const uint32_t nval_max = 1u << (16 - 16 % n);   // largest 2^(k n) with k n <= 16
-    if (!a.count_splits && nval_max >= 512) {
-        const uint64_t want = 4 * 152;
+    if (!a.count_splits) {
         while (vz < 256 && base_ctas * vz < want && nval_max / (vz * 2) >= 256) vz *= 2;
     }
     a.vchunk = (nval_max + vz - 1) / vz;
