@@ -57,7 +57,7 @@ def parse():
                     help="census5:F -- run the K n=5 layer of the first F five-world formulas twice "
                          "(a warm-up and the launch an ncu capture selects with -s 1 -c 1), then exit; "
                          "separation:P -- the same for the first P separation pairs at n=6; "
-                         "stress:P -- the first P mining candidates on 2^13 12-world relations (two "
+                         "stress:P -- the first P mining candidates on 2^16 12-world relations (two "
                          "stress_kernel launches per run: constant pairs, then pairs with a variable)")
     ap.add_argument("--relations", type=int, default=1 << 18,
                     help="relations per generator and size (--workload adversarial)")
@@ -574,7 +574,7 @@ def run_profile_case(spec):
         # pairs on 12-world Erdos-Renyi relations, every relation and valuation
         pairs = [(a, b) for a, b, _ in W.mining_candidates()[:count]]
         sj = E.StressJob(pairs)
-        rels = E.RelationSet.generated("er", 6, 12, 0, 1 << 13)
+        rels = E.RelationSet.generated("er", 6, 12, 0, 1 << 16)
         sj.run(rels, count_splits=True)
         sj.run(rels, count_splits=True)
         torch.cuda.synchronize()
