@@ -87,6 +87,7 @@ def _load():
             lib.orc_template.argtypes = [i32, i32, p]
             lib.orc_stress_relation.argtypes = [i32, u64, i32, u64, p]
             lib.orc_stress_pair.argtypes = [cs, cs, i32, p, u64, ctypes.POINTER(_Stress)]
+            lib.orc_frame_condition.argtypes = [i32, i32, p]
             lib.orc_nvars.argtypes = [cs]
             lib.orc_nodes.argtypes = [cs]
             _lib = lib
@@ -251,3 +252,31 @@ def stress_pair(phi, psi, n, succ):
         raise ValueError("orc_stress_pair rc=%d" % rc)
     split = (int(o.s), int(o.x), int(o.w)) if o.found else None
     return {"split": split, "nsplit": int(o.nsplit), "nvals": int(o.nvals)}
+
+
+CONDITIONS = ("every frame", "no frame", "reflexive", "irreflexive", "serial", "transitive", "symmetric",
+              "Euclidean", "partially functional", "functional", "dense", "directed", "antisymmetric",
+              "asymmetric", "weakly connected", "shift reflexive", "empty relation", "coreflexive")
+
+
+def frame_condition(cond, n):
+    """uint8 array over the K indices of n-world frames: 1 iff the frame
+    satisfies library condition ``cond`` (id or name)."""
+    c = CONDITIONS.index(cond) if isinstance(cond, str) else int(cond)
+    out = np.zeros(1 << (n * n), np.uint8)
+    rc = _load().orc_frame_condition(c, int(n), out.ctypes.data_as(ctypes.c_void_p))
+    if rc:
+        raise ValueError("orc_frame_condition rc=%d" % rc)
+    return out
+
+
+def recover(text, N, conditions=None):
+    """The library conditions whose extension equals the formula's validity
+    set on every frame of 1..N worlds (Sec. 10): names, in library order."""
+    conditions = CONDITIONS if conditions is None else conditions
+    val = [frame_valid_all(text, n) for n in range(1, N + 1)]
+    out = []
+    for c in conditions:
+        if all(np.array_equal(frame_condition(c, n), val[n - 1]) for n in range(1, N + 1)):
+            out.append(c)
+    return out

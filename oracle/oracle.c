@@ -757,3 +757,99 @@ int orc_stress_pair(const char *phi, const char *psi, int n, const uint32_t *suc
     if (best_s != UINT64_MAX) { out->found = 1; out->s = best_s; out->x = best_x; out->w = best_w; }
     return 0;
 }
+
+/* ================================ frame correspondents (Sec. 10, Table 9)
+ *
+ * Recovering a first-order frame condition for a formula compares, over all
+ * frames of at most N worlds, the frames that validate the formula
+ * (orc_frame_valid_all) with the frames that satisfy a condition from a
+ * fixed library.  Each condition below is its first-order definition over
+ * the relation R, written out with quantifiers as loops.  Ids:
+ *    0 every frame             1 no frame               2 reflexive
+ *    3 irreflexive             4 serial                 5 transitive
+ *    6 symmetric               7 Euclidean              8 partially functional
+ *    9 functional             10 dense                 11 directed (confluent)
+ *   12 antisymmetric          13 asymmetric            14 weakly connected
+ *   15 shift reflexive        16 empty relation        17 coreflexive
+ */
+#define ORC_NUM_CONDITIONS 18
+
+static int condition_holds(int c, int n, const uint8_t *R) {
+    int w, v, u, x;
+#define RR(a, b) (R[(a) * n + (b)])
+    switch (c) {
+    case 0: return 1;
+    case 1: return 0;
+    case 2: for (w = 0; w < n; w++) if (!RR(w, w)) return 0; return 1;
+    case 3: for (w = 0; w < n; w++) if (RR(w, w)) return 0; return 1;
+    case 4:                                   /* forall w exists v: wRv */
+        for (w = 0; w < n; w++) {
+            int any = 0;
+            for (v = 0; v < n; v++) any |= RR(w, v);
+            if (!any) return 0;
+        }
+        return 1;
+    case 5: return transitive(n, R);
+    case 6: return symmetric(n, R);
+    case 7:                                   /* wRv and wRu imply vRu */
+        for (w = 0; w < n; w++) for (v = 0; v < n; v++) for (u = 0; u < n; u++)
+            if (RR(w, v) && RR(w, u) && !RR(v, u)) return 0;
+        return 1;
+    case 8:                                   /* wRv and wRu imply v = u */
+        for (w = 0; w < n; w++) for (v = 0; v < n; v++) for (u = 0; u < n; u++)
+            if (RR(w, v) && RR(w, u) && v != u) return 0;
+        return 1;
+    case 9: return condition_holds(4, n, R) && condition_holds(8, n, R);
+    case 10:                                  /* wRv implies exists u: wRu and uRv */
+        for (w = 0; w < n; w++) for (v = 0; v < n; v++) {
+            if (!RR(w, v)) continue;
+            int any = 0;
+            for (u = 0; u < n; u++) any |= RR(w, u) && RR(u, v);
+            if (!any) return 0;
+        }
+        return 1;
+    case 11:                                  /* wRv and wRu imply exists x: vRx and uRx */
+        for (w = 0; w < n; w++) for (v = 0; v < n; v++) for (u = 0; u < n; u++) {
+            if (!(RR(w, v) && RR(w, u))) continue;
+            int any = 0;
+            for (x = 0; x < n; x++) any |= RR(v, x) && RR(u, x);
+            if (!any) return 0;
+        }
+        return 1;
+    case 12:                                  /* wRv and vRw imply w = v */
+        for (w = 0; w < n; w++) for (v = 0; v < n; v++) if (w != v && RR(w, v) && RR(v, w)) return 0;
+        return 1;
+    case 13:                                  /* wRv implies not vRw */
+        for (w = 0; w < n; w++) for (v = 0; v < n; v++) if (RR(w, v) && RR(v, w)) return 0;
+        return 1;
+    case 14:                                  /* wRv and wRu imply vRu or v = u or uRv */
+        for (w = 0; w < n; w++) for (v = 0; v < n; v++) for (u = 0; u < n; u++)
+            if (RR(w, v) && RR(w, u) && !(RR(v, u) || v == u || RR(u, v))) return 0;
+        return 1;
+    case 15:                                  /* wRv implies vRv */
+        for (w = 0; w < n; w++) for (v = 0; v < n; v++) if (RR(w, v) && !RR(v, v)) return 0;
+        return 1;
+    case 16:
+        for (w = 0; w < n * n; w++) if (R[w]) return 0;
+        return 1;
+    case 17:                                  /* wRv implies w = v */
+        for (w = 0; w < n; w++) for (v = 0; v < n; v++) if (w != v && RR(w, v)) return 0;
+        return 1;
+    }
+#undef RR
+    return -1;
+}
+
+/* out[f] = 1 iff the n-world frame with K index f satisfies condition c. */
+int orc_frame_condition(int c, int n, uint8_t *out) {
+    if (n < 1 || n > 5) return -2;
+    if (c < 0 || c >= ORC_NUM_CONDITIONS) return -1;
+    uint64_t nf = (uint64_t)1 << (n * n);
+    #pragma omp parallel for schedule(static, 4096)
+    for (int64_t fi = 0; fi < (int64_t)nf; fi++) {
+        uint8_t R[64];
+        decode_frame((uint64_t)fi, n, R);
+        out[fi] = (uint8_t)condition_holds(c, n, R);
+    }
+    return 0;
+}

@@ -202,3 +202,47 @@ def frames_in_class(cls, n):
 
 def valuation_count(k, n):
     return sum(1 for _ in itertools.product(range(2), repeat=k * n))
+
+
+def condition(name, n, R):
+    """First-order frame conditions of the correspondence library, by
+    direct set comprehension over the relation R (a set of pairs)."""
+    W = range(n)
+    succ = {w: {v for (u, v) in R if u == w} for w in W}
+    if name == "every frame":
+        return True
+    if name == "no frame":
+        return False
+    if name == "reflexive":
+        return all((w, w) in R for w in W)
+    if name == "irreflexive":
+        return not any((w, w) in R for w in W)
+    if name == "serial":
+        return all(succ[w] for w in W)
+    if name == "transitive":
+        return all((w, u) in R for (w, v) in R for u in succ[v])
+    if name == "symmetric":
+        return all((v, w) in R for (w, v) in R)
+    if name == "Euclidean":
+        return all((v, u) in R for w in W for v in succ[w] for u in succ[w])
+    if name == "partially functional":
+        return all(len(succ[w]) <= 1 for w in W)
+    if name == "functional":
+        return all(len(succ[w]) == 1 for w in W)
+    if name == "dense":
+        return all(any(u in succ[w] and v in succ[u] for u in W) for (w, v) in R)
+    if name == "directed":
+        return all(succ[v] & succ[u] for w in W for v in succ[w] for u in succ[w])
+    if name == "antisymmetric":
+        return all(w == v or (v, w) not in R for (w, v) in R)
+    if name == "asymmetric":
+        return all((v, w) not in R for (w, v) in R)
+    if name == "weakly connected":
+        return all(v == u or (v, u) in R or (u, v) in R for w in W for v in succ[w] for u in succ[w])
+    if name == "shift reflexive":
+        return all((v, v) in R for (w, v) in R)
+    if name == "empty relation":
+        return not R
+    if name == "coreflexive":
+        return all(w == v for (w, v) in R)
+    raise ValueError(name)
