@@ -464,6 +464,58 @@ int mk_stress_separate(const mk_program *d_phi, const mk_program *d_psi, int32_t
                        const uint32_t *d_words, const mk_stress_cfg *cfg, uint64_t *d_key,
                        uint32_t *d_nsplit, int32_t *d_status, void *stream);
 
+/* --------------------------------------- frame correspondents (Sec. 10) */
+/* Recovering a first-order frame condition for a formula (Sec. 10, Table
+   9): over every frame of n <= N worlds, the frames that validate the
+   formula (true at every world under every valuation) are compared with
+   the frames that satisfy a condition of a fixed library; a condition
+   whose extension is equal on all of them is the recovered correspondent.
+   Bitmaps are over the K index: bit f%32 of word f/32 is frame f. */
+#define MK_MAX_WORLDS_VALIDITY 5
+enum {
+    MK_COND_ALL = 0,          /* every frame                                */
+    MK_COND_NONE = 1,         /* no frame                                   */
+    MK_COND_REFLEXIVE = 2,    /* wRw                                        */
+    MK_COND_IRREFLEXIVE = 3,  /* not wRw                                    */
+    MK_COND_SERIAL = 4,       /* exists v: wRv                              */
+    MK_COND_TRANSITIVE = 5,   /* wRv, vRu => wRu                            */
+    MK_COND_SYMMETRIC = 6,    /* wRv => vRw                                 */
+    MK_COND_EUCLIDEAN = 7,    /* wRv, wRu => vRu                            */
+    MK_COND_PARTFUNC = 8,     /* wRv, wRu => v = u                          */
+    MK_COND_FUNCTIONAL = 9,   /* exactly one successor                      */
+    MK_COND_DENSE = 10,       /* wRv => exists u: wRu, uRv                  */
+    MK_COND_DIRECTED = 11,    /* wRv, wRu => exists x: vRx, uRx             */
+    MK_COND_ANTISYM = 12,     /* wRv, vRw => w = v                          */
+    MK_COND_ASYM = 13,        /* wRv => not vRw                             */
+    MK_COND_CONNECTED = 14,   /* wRv, wRu => vRu or v = u or uRv            */
+    MK_COND_SHIFTREFL = 15,   /* wRv => vRv                                 */
+    MK_COND_EMPTY = 16,       /* no edge                                    */
+    MK_COND_COREFLEXIVE = 17, /* wRv => w = v                               */
+    MK_NUM_CONDITIONS = 18
+};
+
+/* Words of one n-world bitmap: ceil(2^(n*n) / 32); 0 if n is out of range. */
+uint64_t mk_frame_words(int32_t n);
+
+/* d_bits[p * ld_words + word]: validity bitmap of program p over the
+   n-world frames (1 <= n <= 5), all valuations exhaustive (k*n <= 24, else
+   MK_ST_LIMIT and the row is left unwritten); bits past 2^(n*n) are 0.
+   max_depth: largest program depth (0 = MK_MAX_STACK), as in the census. */
+int mk_frame_validity(const mk_program *d_progs, int32_t nprog, int32_t n, int32_t max_depth,
+                      uint32_t *d_bits, uint64_t ld_words, int32_t *d_status, void *stream);
+
+/* d_bits[c * ld_words + word]: extension of library condition c over the
+   n-world frames, for every c < MK_NUM_CONDITIONS. */
+int mk_frame_conditions(int32_t n, uint32_t *d_bits, uint64_t ld_words, void *stream);
+
+/* d_out[i * nconj + j] = number of frames (set bits among the first
+   `words` words) where row i of d_a differs from the conjunction of rows
+   d_conj[2j] and d_conj[2j+1] of d_b (equal indices: one condition);
+   UINT32_MAX if an index is outside 0..nb-1. */
+int mk_bitmap_mismatch(const uint32_t *d_a, int32_t na, uint64_t lda, const uint32_t *d_b, int32_t nb,
+                       uint64_t ldb, const int32_t *d_conj, int32_t nconj, uint64_t words, uint32_t *d_out,
+                       void *stream);
+
 /* ------------------------------------------------------------- misc */
 const char *mk_strerror(int code);
 int mk_status_error(int32_t status);   /* MK_OK or the MK_E_* for status bits */

@@ -617,6 +617,113 @@ def proposal_experiment(n_formulas=10000, universe=5_467_766, k=1024, train_iden
 
 # ------------------------------------------------------------ sharding
 
+# ---------------------------------------------------- frame correspondents
+def library_entries():
+    """The correspondence library: every condition alone, then every
+    conjunction of two proper conditions (ids >= 2).  Returns
+    ((c1, c2) pairs, names)."""
+    conj, names = [], []
+    nc = len(mk.CONDITION_NAMES)
+    for c in range(nc):
+        conj.append((c, c))
+        names.append(mk.CONDITION_NAMES[c])
+    for a in range(2, nc):
+        for b in range(a + 1, nc):
+            conj.append((a, b))
+            names.append(mk.CONDITION_NAMES[a] + " & " + mk.CONDITION_NAMES[b])
+    return conj, names
+
+
+class Correspondence:
+    """Validity bitmaps of a batch of formulas over every K frame of
+    1..N worlds (mk_frame_validity), the condition library's extensions
+    (mk_frame_conditions) and their mismatch counts (mk_bitmap_mismatch):
+    the recovery procedure of Sec. 10."""
+
+    def __init__(self, texts, N=4, device="cuda"):
+        if not torch.cuda.is_available():
+            raise RuntimeError("Correspondence needs a CUDA device (there is no CPU fallback)")
+        self.texts = list(texts)
+        self.N = N
+        self.device = torch.device(device)
+        self.progs = mk.compile_batch(self.texts)
+        self.d_progs = _dev_bytes(self.progs, self.device)
+        self.depth = int(self.progs["depth"].max()) if len(self.progs) else 1
+        self.offs = [0]
+        for n in range(1, N + 1):
+            self.offs.append(self.offs[-1] + mk.frame_words(n))
+        self.words = self.offs[-1]
+        self.conj, self.names = library_entries()
+        self.d_conj = torch.tensor(np.array(self.conj, np.int32).reshape(-1), device=self.device)
+        self.d_status = torch.zeros(1, dtype=torch.int32, device=self.device)
+
+    def validity(self, sizes=None, stream=None):
+        """[nprog, words] int32 device bitmaps, sizes 1..N side by side."""
+        sizes = range(1, self.N + 1) if sizes is None else sizes
+        bits = torch.zeros((len(self.texts), self.words), dtype=torch.int32, device=self.device)
+        for n in sizes:
+            mk.frame_validity_raw(self.d_progs.data_ptr(), len(self.texts), n, self.depth,
+                                  bits.data_ptr() + 4 * self.offs[n - 1], self.words, self.d_status.data_ptr(),
+                                  _stream_ptr(stream))
+        return bits
+
+    def conditions(self, stream=None):
+        bits = torch.zeros((len(mk.CONDITION_NAMES), self.words), dtype=torch.int32, device=self.device)
+        for n in range(1, self.N + 1):
+            mk.frame_conditions_raw(n, bits.data_ptr() + 4 * self.offs[n - 1], self.words, _stream_ptr(stream))
+        return bits
+
+    def mismatch(self, vbits, cbits, size=None, stream=None):
+        """[nprog, entries] mismatch counts over sizes 1..N, or over the
+        one size `size` when given."""
+        off, words = (0, self.words) if size is None else (self.offs[size - 1], mk.frame_words(size))
+        out = torch.empty((vbits.shape[0], len(self.conj)), dtype=torch.int32, device=self.device)
+        mk.bitmap_mismatch_raw(vbits.data_ptr() + 4 * off, vbits.shape[0], vbits.shape[1],
+                               cbits.data_ptr() + 4 * off, cbits.shape[0], cbits.shape[1], self.d_conj.data_ptr(),
+                               len(self.conj), words, out.data_ptr(), _stream_ptr(stream))
+        return out
+
+    def check_status(self):
+        st = int(self.d_status.item())
+        if st:
+            raise mk.MkError(mk.status_error(st), "device status 0x%x" % st)
+
+
+def recover_correspondents(texts, N=4, confirm_n=5, device="cuda"):
+    """Sec. 10 over a batch: for each formula the library entries whose
+    extension equals its validity set on every frame of 1..N worlds.  A
+    formula whose set is constant (all frames or none) is trivial; for the
+    others with a match, the match is re-checked on every frame of
+    confirm_n worlds (None: skipped).  Returns (rows, stats)."""
+    cj = Correspondence(texts, N, device)
+    v = cj.validity()
+    c = cj.conditions()
+    d = cj.mismatch(v, c).cpu().numpy().view(np.uint32)
+    cj.check_status()
+    rows = []
+    for i, t in enumerate(cj.texts):
+        m = np.nonzero(d[i] == 0)[0]
+        names = [cj.names[j] for j in m]
+        trivial = 0 in m or 1 in m
+        near = int(np.argmin(d[i]))
+        rows.append({"formula": t, "matches": names, "match_ids": [int(j) for j in m], "trivial": bool(trivial),
+                     "nearest": cj.names[near], "nearest_mismatch": int(d[i][near]), "confirmed": None})
+    todo = [i for i, r in enumerate(rows) if r["matches"] and not r["trivial"]]
+    if confirm_n and todo:
+        big = Correspondence([texts[i] for i in todo], confirm_n, device)
+        vb = big.validity(sizes=[confirm_n])
+        cb = big.conditions()
+        db = big.mismatch(vb, cb, size=confirm_n).cpu().numpy().view(np.uint32)
+        big.check_status()
+        for r_i, i in enumerate(todo):
+            rows[i]["confirmed"] = all(int(db[r_i][j]) == 0 for j in rows[i]["match_ids"])
+    stats = {"formulas": len(rows), "trivial": sum(r["trivial"] for r in rows),
+             "recovered": sum(1 for r in rows if r["matches"] and not r["trivial"]),
+             "unmatched": sum(1 for r in rows if not r["matches"]),
+             "confirmed": sum(1 for r in rows if r["confirmed"])}
+    return rows, stats
+
+
 # ------------------------------------------------------------ large frames
 class RelationSet:
     """Relations on n <= 16 worlds in device memory, bit-sliced 32 to a

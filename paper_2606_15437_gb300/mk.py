@@ -165,6 +165,13 @@ _SIGS = {
     "mk_stress_separate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                           ctypes.POINTER(mk_stress_cfg), ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p]),
+    "mk_frame_words": (ctypes.c_uint64, [ctypes.c_int32]),
+    "mk_frame_validity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
+    "mk_frame_conditions": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
+    "mk_bitmap_mismatch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p,
+                                          ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
     "mk_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mk_status_error": (ctypes.c_int, [ctypes.c_int32]),
     "mk_version": (ctypes.c_int, []),
@@ -543,3 +550,27 @@ def decode_stress_key(key):
     if key == NO_KEY:
         return None
     return key >> 20, (key >> 4) & 0xFFFF, key & 15
+
+
+# ----------------------------------------------------- frame correspondents
+CONDITION_NAMES = ("every frame", "no frame", "reflexive", "irreflexive", "serial", "transitive", "symmetric",
+                   "Euclidean", "partially functional", "functional", "dense", "directed", "antisymmetric",
+                   "asymmetric", "weakly connected", "shift reflexive", "empty relation", "coreflexive")
+
+
+def frame_words(n):
+    return int(lib().mk_frame_words(int(n)))
+
+
+def frame_validity_raw(d_progs, nprog, n, max_depth, d_bits, ld_words, d_status, stream):
+    _check(lib().mk_frame_validity(d_progs, int(nprog), int(n), int(max_depth), d_bits, int(ld_words), d_status,
+                                   stream), "mk_frame_validity")
+
+
+def frame_conditions_raw(n, d_bits, ld_words, stream):
+    _check(lib().mk_frame_conditions(int(n), d_bits, int(ld_words), stream), "mk_frame_conditions")
+
+
+def bitmap_mismatch_raw(d_a, na, lda, d_b, nb, ldb, d_conj, nconj, words, d_out, stream):
+    _check(lib().mk_bitmap_mismatch(d_a, int(na), int(lda), d_b, int(nb), int(ldb), d_conj, int(nconj), int(words),
+                                    d_out, stream), "mk_bitmap_mismatch")
