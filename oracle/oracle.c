@@ -853,3 +853,32 @@ int orc_frame_condition(int c, int n, uint8_t *out) {
     }
     return 0;
 }
+
+/* ============================== failure-density atlas (Sec. 9, Fig. atlas)
+ *
+ * D_ij = the fraction of (valuation, world) pairs at which formula i is
+ * false on frame j.  The oracle returns the integer numerator for every
+ * n-world frame (K index order); the denominator is 2^(k n) * n, with all
+ * valuations of the formula's k variables. */
+int orc_atlas(const char *text, int n, uint32_t *count, uint64_t *denom) {
+    oform f;
+    if (n < 1 || n > 4) return -2;
+    if (parse(text, &f)) return -1;
+    int k = f.nvars;
+    if (k * n > 16) return -4;
+    uint64_t nf = (uint64_t)1 << (n * n), nval = (uint64_t)1 << (k * n);
+    *denom = nval * (uint64_t)n;
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t fi = 0; fi < (int64_t)nf; fi++) {
+        uint8_t R[64], V[ORC_MAX_VARS * 8], t[8];
+        decode_frame((uint64_t)fi, n, R);
+        uint32_t c = 0;
+        for (uint64_t x = 0; x < nval; x++) {
+            decode_val(x, k, n, V);
+            truth(&f, f.root, n, R, V, t);
+            for (int w = 0; w < n; w++) c += !t[w];
+        }
+        count[fi] = c;
+    }
+    return 0;
+}
