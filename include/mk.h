@@ -69,6 +69,8 @@ extern "C" {
 #define MK_ST_LIMIT 2u       /* exhaustive valuations with k*n > 24           */
 #define MK_ST_INTERNAL 4u    /* class-table size mismatch or similar          */
 #define MK_ST_TIMEOUT 8u     /* a bounded wait gave up                        */
+#define MK_ST_INDEX 16u      /* an index read from device memory was out of  */
+                             /* range (the entry is skipped)                   */
 
 /* ----------------------------------------------------- frame classes */
 #define MK_CLASS_K 1u        /* all frames                                    */
@@ -515,6 +517,59 @@ int mk_frame_conditions(int32_t n, uint32_t *d_bits, uint64_t ld_words, void *st
 int mk_bitmap_mismatch(const uint32_t *d_a, int32_t na, uint64_t lda, const uint32_t *d_b, int32_t nb,
                        uint64_t ldb, const int32_t *d_conj, int32_t nconj, uint64_t words, uint32_t *d_out,
                        void *stream);
+
+/* ------------------------------------------ failure-density atlas (Sec. 9) */
+/* D_ij = the fraction of (valuation, world) pairs at which formula i is
+   false on frame j, over all 2^(n*n) frames (the paper's atlas uses the 512
+   three-world frames); its seriation (centre the columns, order frames by
+   the first principal axis and formulas by their coordinate on it), the
+   adjacent variation A(pi) = sum_i sum_j |D_i,pi(j+1) - D_i,pi(j)| /
+   (B (F-1)), and the 2-D density view (binned points). */
+
+/* d_counts[p * ld + f]: the numerator of D for program p on frame f
+   (1 <= n <= 4); the denominator is 2^(k n) * n with k = the program's
+   nvars (valuations exhaustive, k*n <= 16 else MK_ST_LIMIT). */
+int mk_atlas_counts(const mk_program *d_progs, int32_t nprog, int32_t n, uint32_t *d_counts, uint64_t ld,
+                    int32_t *d_status, void *stream);
+
+/* Column means of D (d_mean[F]) and the centred Gram matrix
+   d_gram[a * F + b] = sum_i (D_ia - m_a)(D_ib - m_b), FP64; d_denom[B]. */
+int mk_atlas_gram(const uint32_t *d_counts, const uint64_t *d_denom, int32_t B, int32_t F, uint64_t ld,
+                  double *d_mean, double *d_gram, void *stream);
+
+/* Leading eigenvector d_v[F] (and its Rayleigh quotient) of the symmetric
+   matrix d_gram, orthogonal to the nprev vectors d_prev[nprev * F], by
+   `iters` power-iteration steps from a fixed start; its largest-magnitude
+   component is positive.  One CTA. */
+size_t mk_power_workspace_size(int32_t F);
+int mk_power_iteration(const double *d_gram, int32_t F, const double *d_prev, int32_t nprev, int32_t iters,
+                       double *d_v, double *d_lambda, void *d_workspace, size_t ws_bytes, void *stream);
+
+/* Formula coordinates d_u[i] = sum_j (D_ij - m_j) v_j. */
+int mk_atlas_project(const uint32_t *d_counts, const uint64_t *d_denom, int32_t B, int32_t F, uint64_t ld,
+                     const double *d_mean, const double *d_v, double *d_u, void *stream);
+
+/* d_order: the indices 0..n-1 sorted by (d_keys[i], i) ascending. */
+size_t mk_sort_workspace_size(int32_t n);
+int mk_sort_keys(const double *d_keys, int32_t n, int32_t *d_order, void *d_workspace, size_t ws_bytes,
+                 void *stream);
+
+/* d_rowsum[i] = sum_j |count_i,perm(j+1) - count_i,perm(j)| (exact; A(pi) =
+   sum_i rowsum_i / denom_i / (B (F-1))).  A perm entry outside 0..F-1 sets
+   MK_ST_INDEX and its term is skipped. */
+int mk_adjacent_variation(const uint32_t *d_counts, int32_t B, int32_t F, uint64_t ld, const int32_t *d_perm,
+                          uint64_t *d_rowsum, int32_t *d_status, void *stream);
+
+/* d_hist[G * G] (cleared first): point i falls in column
+   floor((x_i - lo) / (hi - lo) * G) and row floor((y_i - lo) / (hi - lo) * G),
+   in FP64, clamped to 0..G-1 (NaN to 0). */
+int mk_histogram2d(const double *d_x, const double *d_y, int64_t npts, double lo, double hi, int32_t G,
+                   uint32_t *d_hist, void *stream);
+
+/* d_stats[4] = occupied cells, largest cell, points in cells holding more
+   than one point, cells within Chebyshev distance `radius` of an occupied
+   cell (the pixels square marks of that radius would cover). */
+int mk_histogram_stats(const uint32_t *d_hist, int32_t G, int32_t radius, uint64_t *d_stats, void *stream);
 
 /* ------------------------------------------------------------- misc */
 const char *mk_strerror(int code);

@@ -28,6 +28,7 @@ extern "C" int mk_status_error(int32_t status) {
     if (status & MK_ST_INTERNAL) return MK_E_INTERNAL;
     if (status & MK_ST_PROGRAM) return MK_E_PROGRAM;
     if (status & MK_ST_LIMIT) return MK_E_LIMIT;
+    if (status & MK_ST_INDEX) return MK_E_ARG;
     return MK_E_INTERNAL;
 }
 

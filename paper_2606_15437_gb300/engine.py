@@ -724,6 +724,102 @@ def recover_correspondents(texts, N=4, confirm_n=5, device="cuda"):
     return rows, stats
 
 
+# ---------------------------------------------------- failure-density atlas
+class Atlas:
+    """The failure-density atlas of Sec. 9 for a batch of formulas over all
+    n-world frames: exact counts (mk_atlas_counts), seriation by the first
+    principal axis (mk_atlas_gram, mk_power_iteration, mk_atlas_project,
+    mk_sort_keys), adjacent variation (mk_adjacent_variation) and the binned
+    density view (mk_histogram2d, mk_histogram_stats)."""
+
+    def __init__(self, texts, n=3, device="cuda"):
+        if not torch.cuda.is_available():
+            raise RuntimeError("Atlas needs a CUDA device (there is no CPU fallback)")
+        self.texts = list(texts)
+        self.B, self.n, self.F = len(self.texts), n, 1 << (n * n)
+        self.device = torch.device(device)
+        self.progs = mk.compile_batch(self.texts)
+        self.d_progs = _dev_bytes(self.progs, self.device)
+        k = self.progs["nvars"].astype(np.uint64)
+        self.denom = (np.uint64(1) << (k * np.uint64(n))) * np.uint64(n)
+        self.d_denom = torch.from_numpy(self.denom.view(np.int64).copy()).to(self.device)
+        self.d_status = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.counts = None
+
+    def check_status(self):
+        st = int(self.d_status.item())
+        if st:
+            raise mk.MkError(mk.status_error(st), "device status 0x%x" % st)
+
+    def compute(self, stream=None):
+        self.counts = torch.empty((self.B, self.F), dtype=torch.int32, device=self.device)
+        mk.atlas_counts_raw(self.d_progs.data_ptr(), self.B, self.n, self.counts.data_ptr(), self.F,
+                            self.d_status.data_ptr(), _stream_ptr(stream))
+        return self.counts
+
+    def principal_axes(self, k=1, iters=4000, stream=None):
+        """The first k principal axes of the centred D (frame loadings, [k, F])
+        and the formula coordinates on them ([k, B]), FP64 on the device."""
+        sp = _stream_ptr(stream)
+        F, B = self.F, self.B
+        self.d_mean = torch.empty(F, dtype=torch.float64, device=self.device)
+        gram = torch.empty((F, F), dtype=torch.float64, device=self.device)
+        mk.atlas_gram_raw(self.counts.data_ptr(), self.d_denom.data_ptr(), B, F, F, self.d_mean.data_ptr(),
+                          gram.data_ptr(), sp)
+        V = torch.empty((k, F), dtype=torch.float64, device=self.device)
+        U = torch.empty((k, B), dtype=torch.float64, device=self.device)
+        lam = torch.empty(k, dtype=torch.float64, device=self.device)
+        ws = torch.empty(mk.power_workspace_size(F), dtype=torch.uint8, device=self.device)
+        for a in range(k):
+            mk.power_iteration_raw(gram.data_ptr(), F, V.data_ptr(), a, iters, V[a].data_ptr(), lam[a].data_ptr(),
+                                   ws.data_ptr(), ws.numel(), sp)
+            mk.atlas_project_raw(self.counts.data_ptr(), self.d_denom.data_ptr(), B, F, F, self.d_mean.data_ptr(),
+                                 V[a].data_ptr(), U[a].data_ptr(), sp)
+        self.gram, self.lam = gram, lam
+        return V, U
+
+    def order(self, keys, stream=None):
+        """Indices sorted by (key, index) on the device."""
+        n = keys.numel()
+        out = torch.empty(n, dtype=torch.int32, device=self.device)
+        ws = torch.empty(mk.sort_workspace_size(n), dtype=torch.uint8, device=self.device)
+        mk.sort_keys_raw(keys.data_ptr(), n, out.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(stream))
+        return out
+
+    def adjacent_variation(self, perm, stream=None):
+        """A(perm), from exact per-row integer sums."""
+        d_perm = perm if torch.is_tensor(perm) else torch.tensor(np.asarray(perm, np.int32), device=self.device)
+        rs = torch.empty(self.B, dtype=torch.int64, device=self.device)
+        mk.adjacent_variation_raw(self.counts.data_ptr(), self.B, self.F, self.F, d_perm.data_ptr(), rs.data_ptr(),
+                                  self.d_status.data_ptr(), _stream_ptr(stream))
+        r = rs.cpu().numpy().view(np.uint64)
+        self.check_status()
+        return float(np.sum(r.astype(np.float64) / self.denom.astype(np.float64)) / (self.B * (self.F - 1)))
+
+    def seriation(self, iters=4000):
+        """(frame order, formula order, axis, coordinates) on the device."""
+        V, U = self.principal_axes(1, iters)
+        return self.order(V[0]), self.order(U[0]), V[0], U[0]
+
+
+def density_view(x, y, lo, hi, G=1024, radius=2, device="cuda"):
+    """Datashading statistics of points (x_i, y_i) binned on a G x G grid
+    (Sec. 9): occupied cells, largest cell, points sharing a cell, the
+    pixels square marks of the given radius cover, and the overdraw
+    factor of drawing every point as such a mark."""
+    hist = torch.empty((G, G), dtype=torch.int32, device=device)
+    mk.histogram2d_raw(x.data_ptr(), y.data_ptr(), x.numel(), lo, hi, G, hist.data_ptr(), _stream_ptr(None))
+    st = torch.empty(4, dtype=torch.int64, device=device)
+    mk.histogram_stats_raw(hist.data_ptr(), G, radius, st.data_ptr(), _stream_ptr(None))
+    occ, big, shared, covered = (int(v) for v in st.cpu().numpy().view(np.uint64))
+    npts = x.numel()
+    draws = npts * (2 * radius + 1) ** 2
+    return {"points": npts, "grid": G, "occupied_bins": occ, "largest_bin": big,
+            "shared_fraction": shared / npts if npts else 0.0, "covered_pixels": covered,
+            "point_pixel_draws": draws, "overdraw": draws / covered if covered else 0.0,
+            "draw_op_reduction": npts / occ if occ else 0.0, "hist": hist}
+
+
 # ------------------------------------------------------------ large frames
 class RelationSet:
     """Relations on n <= 16 worlds in device memory, bit-sliced 32 to a

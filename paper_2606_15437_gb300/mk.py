@@ -172,6 +172,26 @@ _SIGS = {
     "mk_bitmap_mismatch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p,
                                           ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int32,
                                           ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
+    "mk_atlas_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
+    "mk_atlas_gram": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "mk_power_workspace_size": (ctypes.c_size_t, [ctypes.c_int32]),
+    "mk_power_iteration": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_size_t, ctypes.c_void_p]),
+    "mk_atlas_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+    "mk_sort_workspace_size": (ctypes.c_size_t, [ctypes.c_int32]),
+    "mk_sort_keys": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_size_t, ctypes.c_void_p]),
+    "mk_adjacent_variation": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "mk_histogram2d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "mk_histogram_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
     "mk_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mk_status_error": (ctypes.c_int, [ctypes.c_int32]),
     "mk_version": (ctypes.c_int, []),
@@ -574,3 +594,47 @@ def frame_conditions_raw(n, d_bits, ld_words, stream):
 def bitmap_mismatch_raw(d_a, na, lda, d_b, nb, ldb, d_conj, nconj, words, d_out, stream):
     _check(lib().mk_bitmap_mismatch(d_a, int(na), int(lda), d_b, int(nb), int(ldb), d_conj, int(nconj), int(words),
                                     d_out, stream), "mk_bitmap_mismatch")
+
+
+# ------------------------------------------------------ failure-density atlas
+def atlas_counts_raw(d_progs, nprog, n, d_counts, ld, d_status, stream):
+    _check(lib().mk_atlas_counts(d_progs, int(nprog), int(n), d_counts, int(ld), d_status, stream), "mk_atlas_counts")
+
+
+def atlas_gram_raw(d_counts, d_denom, B, F, ld, d_mean, d_gram, stream):
+    _check(lib().mk_atlas_gram(d_counts, d_denom, int(B), int(F), int(ld), d_mean, d_gram, stream), "mk_atlas_gram")
+
+
+def power_workspace_size(F):
+    return int(lib().mk_power_workspace_size(int(F)))
+
+
+def power_iteration_raw(d_gram, F, d_prev, nprev, iters, d_v, d_lambda, d_ws, ws_bytes, stream):
+    _check(lib().mk_power_iteration(d_gram, int(F), d_prev, int(nprev), int(iters), d_v, d_lambda, d_ws,
+                                    int(ws_bytes), stream), "mk_power_iteration")
+
+
+def atlas_project_raw(d_counts, d_denom, B, F, ld, d_mean, d_v, d_u, stream):
+    _check(lib().mk_atlas_project(d_counts, d_denom, int(B), int(F), int(ld), d_mean, d_v, d_u, stream),
+           "mk_atlas_project")
+
+
+def sort_workspace_size(n):
+    return int(lib().mk_sort_workspace_size(int(n)))
+
+
+def sort_keys_raw(d_keys, n, d_order, d_ws, ws_bytes, stream):
+    _check(lib().mk_sort_keys(d_keys, int(n), d_order, d_ws, int(ws_bytes), stream), "mk_sort_keys")
+
+
+def adjacent_variation_raw(d_counts, B, F, ld, d_perm, d_rowsum, d_status, stream):
+    _check(lib().mk_adjacent_variation(d_counts, int(B), int(F), int(ld), d_perm, d_rowsum, d_status, stream),
+           "mk_adjacent_variation")
+
+
+def histogram2d_raw(d_x, d_y, npts, lo, hi, G, d_hist, stream):
+    _check(lib().mk_histogram2d(d_x, d_y, int(npts), float(lo), float(hi), int(G), d_hist, stream), "mk_histogram2d")
+
+
+def histogram_stats_raw(d_hist, G, radius, d_stats, stream):
+    _check(lib().mk_histogram_stats(d_hist, int(G), int(radius), d_stats, stream), "mk_histogram_stats")

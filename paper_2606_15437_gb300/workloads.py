@@ -175,6 +175,18 @@ def census5_formulas(seed=2, count=5621):
     return out + list(AXIOMS)
 
 
+def atlas_formulas(seed=9, count=100000):
+    """The ten-times display corpus of Sec. 9 (deterministically generated):
+    the five-world corpus recipe (length 3-24, depth 1-4, 0-3 variables)
+    drawn `count` times from its own seed."""
+    rng = random.Random(seed)
+    out = []
+    for _ in range(count):
+        L = rng.randint(3, 24)
+        out.append(random_formula(rng, L, rng.randint(1, 4), rng.randint(0, 3)))
+    return out
+
+
 def _log_uniform_int(rng, lo, hi):
     return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
 
