@@ -532,6 +532,8 @@ int mk_bitmap_mismatch(const uint32_t *d_a, int32_t na, uint64_t lda, const uint
 int mk_atlas_counts(const mk_program *d_progs, int32_t nprog, int32_t n, uint32_t *d_counts, uint64_t ld,
                     int32_t *d_status, void *stream);
 
+#define MK_MAX_ATLAS_AXIS 4096   /* frames F for the Gram matrix (n <= 3: 512) */
+
 /* Column means of D (d_mean[F]) and the centred Gram matrix
    d_gram[a * F + b] = sum_i (D_ia - m_a)(D_ib - m_b), FP64; d_denom[B]. */
 int mk_atlas_gram(const uint32_t *d_counts, const uint64_t *d_denom, int32_t B, int32_t F, uint64_t ld,
@@ -539,8 +541,10 @@ int mk_atlas_gram(const uint32_t *d_counts, const uint64_t *d_denom, int32_t B, 
 
 /* Leading eigenvector d_v[F] (and its Rayleigh quotient) of the symmetric
    matrix d_gram, orthogonal to the nprev vectors d_prev[nprev * F], by
-   `iters` power-iteration steps from a fixed start; its largest-magnitude
-   component is positive.  One CTA. */
+   at most `iters` power-iteration steps from a fixed start (fewer once a
+   step moves it by less than 1e-14); its largest-magnitude component is
+   positive.  One CTA; F <= MK_MAX_ATLAS_AXIS.  The workspace is unused
+   (kept for the calling convention; its size may be 0). */
 size_t mk_power_workspace_size(int32_t F);
 int mk_power_iteration(const double *d_gram, int32_t F, const double *d_prev, int32_t nprev, int32_t iters,
                        double *d_v, double *d_lambda, void *d_workspace, size_t ws_bytes, void *stream);

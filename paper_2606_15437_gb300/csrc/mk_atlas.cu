@@ -187,20 +187,24 @@ __global__ void gram_kernel(const uint32_t *counts, const uint64_t *denom, int32
 
 // Leading eigenvector of the symmetric matrix G (F x F) orthogonal to the
 // nprev vectors in prev (F each), by power iteration from a fixed start;
-// one CTA.  Sign: the largest-magnitude component is made positive.
+// one CTA, the iterate in shared memory, one warp per row of G (coalesced
+// reads).  Stops after `iters` steps or once a step moves the unit vector
+// by less than 1e-14 (squared distance 1e-28).  Sign: the largest-magnitude
+// component is made positive.
 __global__ void power_kernel(const double *G, int32_t F, const double *prev, int32_t nprev, int32_t iters,
-                             double *v_out, double *lambda_out, double *work) {
-    double *v = work, *w = work + F;
+                             double *v_out, double *lambda_out) {
+    extern __shared__ __align__(16) double s_pw[];
+    double *v = s_pw, *w = s_pw + F;
     __shared__ double red[32];
     __shared__ double s_val;
-    const int t = threadIdx.x, nt = blockDim.x;
+    const int t = threadIdx.x, nt = blockDim.x, lane = t & 31, warp = t >> 5, nw = nt >> 5;
     auto block_sum = [&](double x) -> double {
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
         __syncthreads();
-        if ((t & 31) == 0) red[t >> 5] = x;
+        if (lane == 0) red[warp] = x;
         __syncthreads();
         if (t < 32) {
-            double y = t < (nt >> 5) ? red[t] : 0.0;
+            double y = t < nw ? red[t] : 0.0;
             for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xFFFFFFFFu, y, o);
             if (t == 0) s_val = y;
         }
@@ -218,10 +222,12 @@ __global__ void power_kernel(const double *G, int32_t F, const double *prev, int
             for (int j = t; j < F; j += nt) v[j] -= d * prev[(size_t)p * F + j];
             __syncthreads();
         }
-        for (int r = t; r < F; r += nt) {
+        for (int r = warp; r < F; r += nw) {
+            const double *row = G + (size_t)r * F;
             double s = 0.0;
-            for (int j = 0; j < F; ++j) s += G[(size_t)r * F + j] * v[j];
-            w[r] = s;
+            for (int j = lane; j < F; j += 32) s += row[j] * v[j];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+            if (lane == 0) w[r] = s;
         }
         __syncthreads();
         double nn = 0.0, vw = 0.0;
@@ -233,8 +239,14 @@ __global__ void power_kernel(const double *G, int32_t F, const double *prev, int
         vw = block_sum(vw);
         lam = vw;
         const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
-        for (int j = t; j < F; j += nt) v[j] = w[j] * inv;
-        __syncthreads();
+        double dd = 0.0;
+        for (int j = t; j < F; j += nt) {
+            const double x = w[j] * inv;
+            dd += (x - v[j]) * (x - v[j]);
+            v[j] = x;
+        }
+        dd = block_sum(dd);
+        if (it >= 16 && dd < 1e-28) break;
     }
     // sign convention
     if (t == 0) {
@@ -406,7 +418,8 @@ extern "C" int mk_atlas_counts(const mk_program *d_progs, int32_t nprog, int32_t
 
 extern "C" int mk_atlas_gram(const uint32_t *d_counts, const uint64_t *d_denom, int32_t B, int32_t F, uint64_t ld,
                              double *d_mean, double *d_gram, void *stream) {
-    if (B < 1 || F < 1 || ld < (uint64_t)F || !d_counts || !d_denom || !d_mean || !d_gram) return MK_E_ARG;
+    if (B < 1 || F < 1 || F > MK_MAX_ATLAS_AXIS || ld < (uint64_t)F || !d_counts || !d_denom || !d_mean || !d_gram)
+        return MK_E_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     colmean_kernel<<<(F + 255) / 256, 256, 0, s>>>(d_counts, d_denom, B, F, ld, d_mean);
     dim3 grid((F + 31) / 32, (F + 31) / 32);
@@ -418,10 +431,17 @@ extern "C" size_t mk_power_workspace_size(int32_t F) { return F > 0 ? (size_t)2 
 
 extern "C" int mk_power_iteration(const double *d_gram, int32_t F, const double *d_prev, int32_t nprev, int32_t iters,
                                   double *d_v, double *d_lambda, void *d_workspace, size_t ws_bytes, void *stream) {
-    if (F < 1 || nprev < 0 || iters < 1 || !d_gram || !d_v || !d_lambda || (nprev && !d_prev)) return MK_E_ARG;
-    if (!d_workspace || ws_bytes < mk_power_workspace_size(F)) return MK_E_WORKSPACE;
-    power_kernel<<<1, 512, 0, (cudaStream_t)stream>>>(d_gram, F, d_prev, nprev, iters, d_v, d_lambda,
-                                                      (double *)d_workspace);
+    (void)d_workspace;
+    (void)ws_bytes;
+    if (F < 1 || F > MK_MAX_ATLAS_AXIS || nprev < 0 || iters < 1 || !d_gram || !d_v || !d_lambda || (nprev && !d_prev))
+        return MK_E_ARG;
+    const size_t sm = 2 * (size_t)F * sizeof(double);
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(power_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * MK_MAX_ATLAS_AXIS * sizeof(double)));
+    });
+    power_kernel<<<1, 1024, sm, (cudaStream_t)stream>>>(d_gram, F, d_prev, nprev, iters, d_v, d_lambda);
     return cudaGetLastError() == cudaSuccess ? MK_OK : MK_E_CUDA;
 }
 
