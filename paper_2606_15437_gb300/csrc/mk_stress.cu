@@ -44,23 +44,28 @@ constexpr int ST_BLOCK = 256;
 constexpr int ST_MAX_TILE = 64;
 constexpr int ST_KEY_X = 4, ST_KEY_S = 20;   // key = s << 20 | x << 4 | w
 
-// World-split layout of n = N worlds.
-template <int N>
+// World-split layout of n = N worlds, W worlds per thread: a group of
+// T = ceil(N/W) threads holds one relation block; thread j holds worlds
+// j*W .. j*W+W-1 (worlds >= N are padding: no edges, never reported).
+template <int N, int W>
 struct WS {
-    static constexpr int GW = 32 / N;               // groups per warp
-    static constexpr int RN = (N + 3) & ~3;         // exchange row of a group (16-byte multiple)
-    static constexpr int XW = (31 / N + 1) * RN;    // exchange words per warp and unit (idle lanes too)
+    static constexpr int T = (N + W - 1) / W;       // threads per group
+    static constexpr int GW = 32 / T;               // groups per warp
+    static constexpr int RN = (T * W + 3) & ~3;     // exchange row of a group (16-byte multiple)
+    static constexpr int XW = (31 / T + 1) * RN;    // exchange words per warp and unit (idle lanes too)
 };
 
 // Units per dispatched instruction: UB relation blocks x V valuations.
 // Constant pairs have one valuation, so their launch walks UB0 blocks;
-// pairs with variables walk UB1 blocks under V consecutive valuations each
-// (the edge registers of a block serve all V valuations).
+// pairs with variables walk one block under V consecutive valuations
+// (the edge registers of a block serve all V valuations).  W: worlds per
+// thread, 2 where it fills more lanes (11 and 12 worlds).
 template <int N>
 constexpr int st_ub0() { return N <= 5 ? 8 : N <= 8 ? 6 : 4; }
 template <int N>
-constexpr int st_ub1() { return 1; }
-constexpr int ST_V = 16;
+constexpr int st_w1() { return (N == 11 || N == 12) ? 2 : 1; }
+template <int N>
+constexpr int st_v1() { return st_w1<N>() == 2 ? 8 : 16; }
 
 struct StressArgs {
     const mk_program *phi;
@@ -80,41 +85,43 @@ struct StressArgs {
     int32_t *status;
 };
 
-template <int N, int U, int BLOCK>
+template <int N, int W, int U, int BLOCK>
 struct StressSmem {
     static constexpr size_t code_bytes(int tile) { return ((size_t)tile * ST_OPS_STRIDE * 6 + 15) & ~(size_t)15; }
     // na, nb, k, count (4 x 4 B) + key (8 B) per pair, rounded to 16 bytes
     static constexpr size_t meta_bytes(int tile) { return ((size_t)tile * 24 + 15) & ~(size_t)15; }
-    static constexpr size_t stack_bytes() { return (size_t)MK_MAX_STACK * U * BLOCK * 4; }
-    static constexpr size_t xbuf_bytes() { return (size_t)(BLOCK / 32) * U * WS<N>::XW * 4; }
+    static constexpr size_t stack_bytes() { return (size_t)MK_MAX_STACK * U * W * BLOCK * 4; }
+    static constexpr size_t xbuf_bytes() { return (size_t)(BLOCK / 32) * U * WS<N, W>::XW * 4; }
     static size_t total(int tile) { return code_bytes(tile) + meta_bytes(tile) + stack_bytes() + xbuf_bytes(); }
 };
 
 // Decode for the world-split interpreter: stack operands scaled to the
-// thread's stack column (d -> d*U*BLOCK), variable operands to the bit
+// thread's stack column (d -> d*U*W*BLOCK), variable operands to the bit
 // offset of p_i in a valuation (i -> i*N).
-template <int N, int U, int BLOCK>
+template <int N, int SW, int BLOCK>
 __device__ __forceinline__ void decode_ws(const mk_program &p, uint8_t *ops, uint16_t *offs) {
     for (int i = 0; i < p.n_instr; ++i) {
         const int op = p.code[i] & 15, arg = p.code[i] >> 4;
         ops[i] = (uint8_t)op;
         const bool stack_op = op >= MK_OP_PUSH && op <= MK_OP_IFF_S;
-        offs[i] = (uint16_t)(stack_op ? arg * (U * BLOCK) : arg * N);
+        offs[i] = (uint16_t)(stack_op ? arg * (SW * BLOCK) : arg * N);
     }
     ops[p.n_instr] = (uint8_t)MK_OP_END;
     offs[p.n_instr] = 0;
 }
 
 // One modal step for all U = UB*V units (unit u: block u/V): publish this
-// world's word, read the group's n words, combine with this world's edge
-// row of the unit's block.
-template <int N, int UB, int V, bool BOX>
-__device__ __forceinline__ void modal_ws(uint32_t (&A)[UB * V], const uint32_t (&E)[UB][N], uint32_t *xw, int xo,
-                                         int j, bool active) {
-    constexpr int RN = WS<N>::RN, XW = WS<N>::XW, U = UB * V;
+// thread's W world words, read the group's words, combine with this
+// thread's edge rows of the unit's block.
+template <int N, int W, int UB, int V, bool BOX>
+__device__ __forceinline__ void modal_ws(uint32_t (&A)[UB * V][W], const uint32_t (&E)[UB][W][N], uint32_t *xw,
+                                         int xo, int jw0, bool active) {
+    constexpr int RN = WS<N, W>::RN, XW = WS<N, W>::XW, U = UB * V;
 #pragma unroll
     for (int u = 0; u < U; ++u)
-        if (active) xw[u * XW + xo + j] = A[u];
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            if (active) xw[u * XW + xo + jw0 + w] = A[u][w];
     __syncwarp();
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -128,95 +135,99 @@ __device__ __forceinline__ void modal_ws(uint32_t (&A)[UB * V], const uint32_t (
             t[4 * q + 2] = v.z;
             t[4 * q + 3] = v.w;
         }
-        uint32_t acc = BOX ? 0xFFFFFFFFu : 0u;
 #pragma unroll
-        for (int v = 0; v < N; ++v) {
-            if (BOX) acc &= t[v] | ~E[u / V][v];
-            else acc |= t[v] & E[u / V][v];
+        for (int w = 0; w < W; ++w) {
+            uint32_t acc = BOX ? 0xFFFFFFFFu : 0u;
+#pragma unroll
+            for (int v = 0; v < N; ++v) {
+                if (BOX) acc &= t[v] | ~E[u / V][w][v];
+                else acc |= t[v] & E[u / V][w][v];
+            }
+            A[u][w] = acc;
         }
-        A[u] = acc;
     }
     __syncwarp();
 }
 
-// Run a decoded program on this thread's world of U = UB*V units, unit u
-// being block u/V under valuation x + u%V (xj[v] = (x + v) >> j).  Every
-// thread of a warp runs the same program, so the __syncwarp of the modal
-// steps is reached by all 32 lanes.
-template <int N, int UB, int V, int BLOCK>
-__device__ __forceinline__ void run_ws(const uint8_t *ops, const uint16_t *offs, const uint32_t (&xj)[V],
-                                       const uint32_t (&E)[UB][N], uint32_t *stack, uint32_t *xw, int xo, int j,
-                                       bool active, uint32_t (&A)[UB * V]) {
+// Run a decoded program on this thread's W worlds of U = UB*V units, unit
+// u being block u/V under valuation x + u%V (xs[v] = (x + v) >> jw0).
+// Every thread of a warp runs the same program, so the __syncwarp of the
+// modal steps is reached by all 32 lanes.
+template <int N, int W, int UB, int V, int BLOCK>
+__device__ __forceinline__ void run_ws(const uint8_t *ops, const uint16_t *offs, const uint32_t (&xs)[V],
+                                       const uint32_t (&E)[UB][W][N], uint32_t *stack, uint32_t *xw, int xo, int jw0,
+                                       bool active, uint32_t (&A)[UB * V][W]) {
     constexpr int U = UB * V;
     uint32_t op = ops[0], off = offs[0];
     for (int pc = 1;; ++pc) {
         const uint32_t op_next = ops[pc], off_next = offs[pc];
         uint32_t *st = stack + off;
-        // atom truth word of p_i at this world under unit u's valuation:
+        // atom truth word of p_i at world jw0+w under unit u's valuation:
         // only variable operands (off = i*N < 16) are shifts
-#define MK_ATOM(u) (0u - ((xj[(u) % V] >> off) & 1u))
+#define MK_ATOM(u, w) (0u - ((xs[(u) % V] >> (off + (w))) & 1u))
+#define MK_EACH for (int u = 0; u < U; ++u) _Pragma("unroll") for (int w = 0; w < W; ++w)
         switch (op) {
         case MK_OP_LDV:
 #pragma unroll
-            for (int u = 0; u < U; ++u) A[u] = MK_ATOM(u);
+            MK_EACH A[u][w] = MK_ATOM(u, w);
             break;
         case MK_OP_LDT:
 #pragma unroll
-            for (int u = 0; u < U; ++u) A[u] = 0xFFFFFFFFu;
+            MK_EACH A[u][w] = 0xFFFFFFFFu;
             break;
         case MK_OP_LDF:
 #pragma unroll
-            for (int u = 0; u < U; ++u) A[u] = 0u;
+            MK_EACH A[u][w] = 0u;
             break;
         case MK_OP_NOT:
 #pragma unroll
-            for (int u = 0; u < U; ++u) A[u] = ~A[u];
+            MK_EACH A[u][w] = ~A[u][w];
             break;
         case MK_OP_BOX:
-            modal_ws<N, UB, V, true>(A, E, xw, xo, j, active);
+            modal_ws<N, W, UB, V, true>(A, E, xw, xo, jw0, active);
             break;
         case MK_OP_DIA:
-            modal_ws<N, UB, V, false>(A, E, xw, xo, j, active);
+            modal_ws<N, W, UB, V, false>(A, E, xw, xo, jw0, active);
             break;
         case MK_OP_PUSH:
 #pragma unroll
-            for (int u = 0; u < U; ++u) st[u * BLOCK] = A[u];
+            MK_EACH st[(u * W + w) * BLOCK] = A[u][w];
             break;
         case MK_OP_AND_S:
 #pragma unroll
-            for (int u = 0; u < U; ++u) A[u] &= st[u * BLOCK];
+            MK_EACH A[u][w] &= st[(u * W + w) * BLOCK];
             break;
         case MK_OP_OR_S:
 #pragma unroll
-            for (int u = 0; u < U; ++u) A[u] |= st[u * BLOCK];
+            MK_EACH A[u][w] |= st[(u * W + w) * BLOCK];
             break;
         case MK_OP_IMP_S:
 #pragma unroll
-            for (int u = 0; u < U; ++u) A[u] = ~st[u * BLOCK] | A[u];
+            MK_EACH A[u][w] = ~st[(u * W + w) * BLOCK] | A[u][w];
             break;
         case MK_OP_RIMP_S:
 #pragma unroll
-            for (int u = 0; u < U; ++u) A[u] = ~A[u] | st[u * BLOCK];
+            MK_EACH A[u][w] = ~A[u][w] | st[(u * W + w) * BLOCK];
             break;
         case MK_OP_IFF_S:
 #pragma unroll
-            for (int u = 0; u < U; ++u) A[u] = ~(A[u] ^ st[u * BLOCK]);
+            MK_EACH A[u][w] = ~(A[u][w] ^ st[(u * W + w) * BLOCK]);
             break;
         case MK_OP_AND_V:
 #pragma unroll
-            for (int u = 0; u < U; ++u) A[u] &= MK_ATOM(u);
+            MK_EACH A[u][w] &= MK_ATOM(u, w);
             break;
         case MK_OP_OR_V:
 #pragma unroll
-            for (int u = 0; u < U; ++u) A[u] |= MK_ATOM(u);
+            MK_EACH A[u][w] |= MK_ATOM(u, w);
             break;
         case MK_OP_IMP_V:
 #pragma unroll
-            for (int u = 0; u < U; ++u) A[u] = ~A[u] | MK_ATOM(u);
+            MK_EACH A[u][w] = ~A[u][w] | MK_ATOM(u, w);
             break;
         case MK_OP_RIMP_V:
 #pragma unroll
-            for (int u = 0; u < U; ++u) A[u] = ~MK_ATOM(u) | A[u];
+            MK_EACH A[u][w] = ~MK_ATOM(u, w) | A[u][w];
             break;
         case MK_OP_END:
             return;
@@ -226,14 +237,15 @@ __device__ __forceinline__ void run_ws(const uint8_t *ops, const uint16_t *offs,
         op = op_next;
         off = off_next;
     }
+#undef MK_EACH
 #undef MK_ATOM
 }
 
-template <int N, int UB, int V, int BLOCK>
+template <int N, int W, int UB, int V, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 2) stress_kernel(StressArgs a) {
     constexpr int U = UB * V;
-    using SM = StressSmem<N, U, BLOCK>;
-    using L = WS<N>;
+    using SM = StressSmem<N, W, U, BLOCK>;
+    using L = WS<N, W>;
     constexpr int GROUPS = (BLOCK / 32) * L::GW;
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int s_active;
@@ -248,10 +260,11 @@ __global__ void __launch_bounds__(BLOCK, 2) stress_kernel(StressArgs a) {
     uint32_t *s_cnt = (uint32_t *)(s_k + tile);
     unsigned long long *s_key = (unsigned long long *)(s_cnt + tile);
     uint32_t *s_stack = (uint32_t *)(smem + SM::code_bytes(tile) + SM::meta_bytes(tile));
-    uint32_t *s_xbuf = s_stack + (size_t)MK_MAX_STACK * U * BLOCK;
+    uint32_t *s_xbuf = s_stack + (size_t)MK_MAX_STACK * U * W * BLOCK;
 
     const int tid = threadIdx.x, wi = tid >> 5, lane = tid & 31;
-    const int g = lane / N, j = lane - g * N;
+    const int g = lane / L::T, j = lane - g * L::T;
+    const int jw0 = j * W;                         // this thread's first world
     const bool active = g < L::GW;
     const int G = wi * L::GW + (active ? g : 0);
     const uint64_t cta_b0 = a.blk_lo + (uint64_t)blockIdx.x * GROUPS * UB;
@@ -282,31 +295,40 @@ __global__ void __launch_bounds__(BLOCK, 2) stress_kernel(StressArgs a) {
         s_key[i] = ~0ull;
         if (ok) {
             atomicAdd(&s_active, 1);
-            decode_ws<N, U, BLOCK>(pa, s_ops_a + i * ST_OPS_STRIDE, s_offs_a + i * ST_OPS_STRIDE);
-            decode_ws<N, U, BLOCK>(pb, s_ops_b + i * ST_OPS_STRIDE, s_offs_b + i * ST_OPS_STRIDE);
+            decode_ws<N, U * W, BLOCK>(pa, s_ops_a + i * ST_OPS_STRIDE, s_offs_a + i * ST_OPS_STRIDE);
+            decode_ws<N, U * W, BLOCK>(pb, s_ops_b + i * ST_OPS_STRIDE, s_offs_b + i * ST_OPS_STRIDE);
         }
     }
     __syncthreads();
     if (s_active == 0) return;
 
-    // this thread's rows of its UB relation blocks
-    uint32_t E[UB][N];
+    // this thread's rows of its UB relation blocks (padding worlds: none)
+    uint32_t E[UB][W][N];
     uint32_t valid[UB];
 #pragma unroll
     for (int b = 0; b < UB; ++b) {
         const uint64_t blk = cta_b0 + (uint64_t)G * UB + b;
         valid[b] = 0;
-        if (active && blk < a.nblocks) {
-            const uint32_t *row = a.words + (blk * N + j) * N;
-#pragma unroll
-            for (int v = 0; v < N; ++v) E[b][v] = row[v];
+        const bool have = active && blk < a.nblocks;
+        if (have) {
             const uint64_t left = a.count - (blk << 5);
             valid[b] = left >= 32 ? 0xFFFFFFFFu : ((1u << left) - 1u);
-        } else {
+        }
 #pragma unroll
-            for (int v = 0; v < N; ++v) E[b][v] = 0u;
+        for (int w = 0; w < W; ++w) {
+            if (have && jw0 + w < N) {
+                const uint32_t *row = a.words + (blk * N + (uint64_t)(jw0 + w)) * N;
+#pragma unroll
+                for (int v = 0; v < N; ++v) E[b][w][v] = row[v];
+            } else {
+#pragma unroll
+                for (int v = 0; v < N; ++v) E[b][w][v] = 0u;
+            }
         }
     }
+    uint32_t wmask[W];                            // real worlds of this thread
+#pragma unroll
+    for (int w = 0; w < W; ++w) wmask[w] = jw0 + w < N ? 0xFFFFFFFFu : 0u;
     uint32_t *xw = s_xbuf + (size_t)wi * U * L::XW;
     const int xo = g * L::RN;
     uint32_t *stk = s_stack + tid;
@@ -317,28 +339,34 @@ __global__ void __launch_bounds__(BLOCK, 2) stress_kernel(StressArgs a) {
         const uint32_t x_hi = min(nval, x_lo + a.vchunk);
         const uint8_t *oa = s_ops_a + fi * ST_OPS_STRIDE, *ob = s_ops_b + fi * ST_OPS_STRIDE;
         const uint16_t *fa = s_offs_a + fi * ST_OPS_STRIDE, *fb = s_offs_b + fi * ST_OPS_STRIDE;
-        int best_o = UB * 32;
+        int best_o = UB * 32, best_w = 0;
         uint32_t best_x = 0;
         uint32_t hm[UB];
 #pragma unroll
         for (int b = 0; b < UB; ++b) hm[b] = 0;
         for (uint32_t x = x_lo; x < x_hi; x += V) {
-            uint32_t A[U], B[U], xj[V];
+            uint32_t A[U][W], B[U][W], xs[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) xj[v] = (x + v) >> j;
-            run_ws<N, UB, V, BLOCK>(oa, fa, xj, E, stk, xw, xo, j, active, A);
-            run_ws<N, UB, V, BLOCK>(ob, fb, xj, E, stk, xw, xo, j, active, B);
-            // blocks outer, valuations inner: for one relation the first
-            // unit with a difference has the least valuation
+            for (int v = 0; v < V; ++v) xs[v] = (x + v) >> jw0;
+            run_ws<N, W, UB, V, BLOCK>(oa, fa, xs, E, stk, xw, xo, jw0, active, A);
+            run_ws<N, W, UB, V, BLOCK>(ob, fb, xs, E, stk, xw, xo, jw0, active, B);
+            // blocks outer, valuations inner, worlds ascending: for one
+            // relation the first difference found has the least valuation,
+            // then the least world
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const uint32_t d = (x + (u % V) < x_hi) ? (A[u] ^ B[u]) & valid[u / V] : 0u;
-                hm[u / V] |= d;
-                if (d) {
-                    const int o = (u / V) * 32 + __ffs(d) - 1;
-                    if (o < best_o) {
-                        best_o = o;
-                        best_x = x + (u % V);
+                const uint32_t vm = (x + (u % V) < x_hi) ? valid[u / V] : 0u;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    const uint32_t d = (A[u][w] ^ B[u][w]) & vm & wmask[w];
+                    hm[u / V] |= d;
+                    if (d) {
+                        const int o = (u / V) * 32 + __ffs(d) - 1;
+                        if (o < best_o) {
+                            best_o = o;
+                            best_x = x + (u % V);
+                            best_w = w;
+                        }
                     }
                 }
             }
@@ -346,7 +374,8 @@ __global__ void __launch_bounds__(BLOCK, 2) stress_kernel(StressArgs a) {
         if (active && best_o < UB * 32) {
             const uint64_t s = a.index_base + ((cta_b0 + (uint64_t)G * UB + (uint64_t)(best_o >> 5)) << 5) +
                                (uint64_t)(best_o & 31);
-            const unsigned long long key = (s << ST_KEY_S) | ((uint64_t)best_x << ST_KEY_X) | (uint64_t)j;
+            const unsigned long long key =
+                (s << ST_KEY_S) | ((uint64_t)best_x << ST_KEY_X) | (uint64_t)(jw0 + best_w);
             atomicMin(&s_key[fi], key);
         }
         if (a.count_splits) {
@@ -361,7 +390,7 @@ __global__ void __launch_bounds__(BLOCK, 2) stress_kernel(StressArgs a) {
                 for (int b = 0; b < UB; ++b) {
                     uint32_t m = 0;
 #pragma unroll
-                    for (int v = 0; v < N; ++v) m |= xw[b * L::XW + xo + v];
+                    for (int t = 0; t < L::T; ++t) m |= xw[b * L::XW + xo + t];
                     c += __popc(m);
                 }
                 if (c) atomicAdd(&s_cnt[fi], c);
@@ -424,11 +453,11 @@ void st_smem(K kern, size_t bytes) {
     g_st_attr.push_back((const void *)kern);
 }
 
-template <int N, int UB, int V>
+template <int N, int W, int UB, int V>
 void launch_stress_kind(StressArgs a, uint64_t blk_hi, uint32_t vz, cudaStream_t s) {
-    constexpr int GROUPS = (ST_BLOCK / 32) * WS<N>::GW;
-    using SM = StressSmem<N, UB * V, ST_BLOCK>;
-    auto kern = stress_kernel<N, UB, V, ST_BLOCK>;
+    constexpr int GROUPS = (ST_BLOCK / 32) * WS<N, W>::GW;
+    using SM = StressSmem<N, W, UB * V, ST_BLOCK>;
+    auto kern = stress_kernel<N, W, UB, V, ST_BLOCK>;
     st_smem(kern, SM::total(ST_MAX_TILE));
     const uint64_t per_cta = (uint64_t)GROUPS * UB;
     // ascending launches of at most 4096 CTAs: pairs split in one launch are
@@ -450,10 +479,10 @@ void launch_stress(StressArgs a, uint64_t blk_hi, uint32_t vz, cudaStream_t s) {
     StressArgs c0 = a;
     c0.with_vars = 0;
     c0.vchunk = 1;
-    launch_stress_kind<N, st_ub0<N>(), 1>(c0, blk_hi, 1, s);
+    launch_stress_kind<N, 1, st_ub0<N>(), 1>(c0, blk_hi, 1, s);
     StressArgs c1 = a;
     c1.with_vars = 1;
-    launch_stress_kind<N, st_ub1<N>(), ST_V>(c1, blk_hi, vz, s);
+    launch_stress_kind<N, st_w1<N>(), 1, st_v1<N>()>(c1, blk_hi, vz, s);
 }
 
 void launch_stress_n(int n, const StressArgs &a, uint64_t blk_hi, uint32_t vz, cudaStream_t s) {
@@ -478,7 +507,7 @@ void launch_stress_n(int n, const StressArgs &a, uint64_t blk_hi, uint32_t vz, c
 }
 
 template <int N>
-uint64_t per_cta_blocks() { return (uint64_t)(ST_BLOCK / 32) * WS<N>::GW * st_ub1<N>(); }
+uint64_t per_cta_blocks() { return (uint64_t)(ST_BLOCK / 32) * WS<N, st_w1<N>()>::GW; }
 
 uint64_t per_cta_n(int n) {
     switch (n) {

@@ -92,7 +92,7 @@ def _oracle(pairs, n, succ):
 
 
 @pytest.mark.parametrize("n,gen,count,k_max", [(1, "er", 77, 2), (3, "er", 700, 2), (6, "scc", 3000, 1),
-                                               (7, "deadend", 1500, 1), (9, "flip", 600, 1),
+                                               (7, "deadend", 1500, 1), (9, "flip", 600, 1), (11, "scc", 700, 1),
                                                (12, "backedge", 100, 1), (12, "permscc", 2500, 0),
                                                (16, "er", 5000, 0), (16, "flip", 70, 1)])
 def test_first_split_and_counts_match_oracle(n, gen, count, k_max):
