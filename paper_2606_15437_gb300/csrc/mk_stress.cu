@@ -59,11 +59,12 @@ struct WS {
 // Constant pairs have one valuation, so their launch walks UB0 blocks;
 // pairs with variables walk one block under V consecutive valuations
 // (the edge registers of a block serve all V valuations).  W: worlds per
-// thread, 2 where it fills more lanes (11 and 12 worlds).
+// thread: 2 from 7 worlds up (more lanes hold a world at 11 and 12, and
+// the group exchange costs half as much per logic op).
 template <int N>
 constexpr int st_ub0() { return N <= 5 ? 8 : N <= 8 ? 6 : 4; }
 template <int N>
-constexpr int st_w1() { return (N == 11 || N == 12) ? 2 : 1; }
+constexpr int st_w1() { return N >= 7 ? 2 : 1; }
 template <int N>
 constexpr int st_v1() { return st_w1<N>() == 2 ? 8 : 16; }
 
