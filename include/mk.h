@@ -395,6 +395,25 @@ int mk_mlp_infer_bf16(const float *d_params, int32_t features, int32_t hidden, c
                       const int32_t *d_pa, const int32_t *d_pb, int32_t batch, float *d_logits,
                       void *d_workspace, size_t ws_bytes, void *stream);
 
+/* The same scoring with the first layer on the 5th-generation tensor cores
+   (tcgen05.mma, BF16 operands in shared memory, FP32 accumulator in tensor
+   memory); features a multiple of 128, hidden 256.  A bounded wait that
+   runs out sets MK_ST_TIMEOUT in *d_status (the logits are then invalid). */
+int mk_mlp_infer_tc(const float *d_params, int32_t features, int32_t hidden, const uint32_t *d_vec,
+                    const int32_t *d_pa, const int32_t *d_pb, int32_t batch, float *d_logits, int32_t *d_status,
+                    void *d_workspace, size_t ws_bytes, void *stream);
+
+/* The first layer alone, h1[i * 256 + h] = relu(x_i . W1[:, h] + b1[h]) with
+   W1 given as BF16 W1^T (d_w1t[h * features + f], from mk_mlp_w1t_bf16):
+   on tcgen05 (features % 128 == 0, 16-byte aligned d_w1t and d_h1) or on
+   warp-level mma.sync (the legacy path, for comparison). */
+int mk_mlp_w1t_bf16(const float *d_params, int32_t features, int32_t hidden, void *d_w1t, void *stream);
+int mk_mlp_layer1_tc(const uint32_t *d_vec, int32_t features, const int32_t *d_pa, const int32_t *d_pb,
+                     int32_t batch, const void *d_w1t, const float *d_b1, float *d_h1, int32_t *d_status,
+                     void *stream);
+int mk_mlp_layer1_mma(const uint32_t *d_vec, int32_t features, const int32_t *d_pa, const int32_t *d_pb,
+                      int32_t batch, const void *d_w1t, const float *d_b1, float *d_h1, void *stream);
+
 /* ------------------------------------------- large frames (Sec. 7) */
 /* Separation beyond the exhaustive sizes runs over explicit relations on up
    to 16 worlds: the 39 stress templates (path, reverse-path, reflexive-path,

@@ -659,3 +659,46 @@ extern "C" int mk_mlp_infer_bf16(const float *d_params, int32_t features, int32_
                                                  nullptr);
     return cudaGetLastError() == cudaSuccess ? MK_OK : MK_E_CUDA;
 }
+
+// W1 (FP32, [features][hidden] in the parameter buffer) as BF16 W1^T.
+extern "C" int mk_mlp_w1t_bf16(const float *d_params, int32_t features, int32_t hidden, void *d_w1t, void *stream) {
+    if (features <= 0 || hidden <= 0 || !d_params || !d_w1t) return MK_E_ARG;
+    MlpView v = mlp_view((float *)d_params, features, hidden);
+    f32_to_bf16_t_kernel<<<1024, 256, 0, (cudaStream_t)stream>>>(v.W1, features, hidden, (__nv_bfloat16 *)d_w1t);
+    return cudaGetLastError() == cudaSuccess ? MK_OK : MK_E_CUDA;
+}
+
+// The first layer with warp-level mma.sync (the legacy tensor-core path),
+// kept as the comparison for mk_mlp_layer1_tc.
+extern "C" int mk_mlp_layer1_mma(const uint32_t *d_vec, int32_t features, const int32_t *d_pa, const int32_t *d_pb,
+                                 int32_t batch, const void *d_w1t, const float *d_b1, float *d_h1, void *stream) {
+    if (features <= 0 || features % 64 || batch < 0) return MK_E_ARG;
+    if (batch == 0) return MK_OK;
+    if (!d_vec || !d_pa || !d_pb || !d_w1t || !d_b1 || !d_h1) return MK_E_ARG;
+    infer_l1_bf16_kernel<<<(batch + IBP - 1) / IBP, 256, 0, (cudaStream_t)stream>>>(
+        d_vec, features / 64, d_pa, d_pb, batch, (const __nv_bfloat16 *)d_w1t, d_b1, d_h1);
+    return cudaGetLastError() == cudaSuccess ? MK_OK : MK_E_CUDA;
+}
+
+extern "C" int mk_mlp_infer_tc(const float *d_params, int32_t features, int32_t hidden, const uint32_t *d_vec,
+                               const int32_t *d_pa, const int32_t *d_pb, int32_t batch, float *d_logits,
+                               int32_t *d_status, void *d_workspace, size_t ws_bytes, void *stream) {
+    if (hidden != IH || features % 128 || batch < 0 || !d_params || !d_vec || !d_logits || !d_status) return MK_E_ARG;
+    if (batch == 0) return MK_OK;
+    if (!d_workspace || ws_bytes < mk_mlp_infer_workspace_size(batch, features, hidden)) return MK_E_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    MlpView v = mlp_view((float *)d_params, features, hidden);
+    float *h1 = (float *)d_workspace, *h2 = h1 + (size_t)batch * hidden;
+    __nv_bfloat16 *w1t = (__nv_bfloat16 *)(h2 + (size_t)batch * hidden);
+    f32_to_bf16_t_kernel<<<1024, 256, 0, s>>>(v.W1, features, hidden, w1t);
+    int rc = mk_mlp_layer1_tc(d_vec, features, d_pa, d_pb, batch, w1t, v.b1, h1, d_status, stream);
+    if (rc != MK_OK) return rc;
+    GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.M = batch; g.N = hidden; g.K = hidden;
+    g.A = h1; g.lda = hidden; g.B = v.W2; g.ldb = hidden; g.C = h2; g.ldc = hidden; g.bias = v.b2; g.relu = 1;
+    gemm<A_ROW, B_ROW>(g, s);
+    head_kernel<<<(batch + 7) / 8, 256, 0, s>>>(h2, v.w3, v.b3, nullptr, nullptr, batch, hidden, d_logits, nullptr,
+                                                 nullptr);
+    return cudaGetLastError() == cudaSuccess ? MK_OK : MK_E_CUDA;
+}

@@ -447,17 +447,28 @@ class MLP:
                            out.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(None))
         return out
 
-    def score(self, vec, pa, pb, batch=65536):
-        """BF16 tensor-core logits for many pairs (mk_mlp_infer_bf16)."""
+    def score(self, vec, pa, pb, batch=65536, impl="tc"):
+        """BF16 tensor-core logits for many pairs: first layer on tcgen05
+        (mk_mlp_infer_tc), or on warp-level mma.sync (impl="mma",
+        mk_mlp_infer_bf16)."""
         n = len(pa)
         out = torch.empty(n, dtype=torch.float32, device=self.dev)
         ws = torch.empty(mk.mlp_infer_workspace_size(min(batch, max(n, 1)), self.F, self.H), dtype=torch.uint8,
                          device=self.dev)
+        status = torch.zeros(1, dtype=torch.int32, device=self.dev)
         for s in range(0, n, batch):
             e = min(n, s + batch)
-            mk.mlp_infer_bf16_raw(self.params.data_ptr(), self.F, self.H, vec.data_ptr(), pa[s:e].data_ptr(),
-                                  pb[s:e].data_ptr(), e - s, out[s:].data_ptr(), ws.data_ptr(), ws.numel(),
-                                  _stream_ptr(None))
+            if impl == "tc":
+                mk.mlp_infer_tc_raw(self.params.data_ptr(), self.F, self.H, vec.data_ptr(), pa[s:e].data_ptr(),
+                                    pb[s:e].data_ptr(), e - s, out[s:].data_ptr(), status.data_ptr(), ws.data_ptr(),
+                                    ws.numel(), _stream_ptr(None))
+            else:
+                mk.mlp_infer_bf16_raw(self.params.data_ptr(), self.F, self.H, vec.data_ptr(), pa[s:e].data_ptr(),
+                                      pb[s:e].data_ptr(), e - s, out[s:].data_ptr(), ws.data_ptr(), ws.numel(),
+                                      _stream_ptr(None))
+        st = int(status.item())
+        if st:
+            raise mk.MkError(mk.status_error(st), "device status 0x%x" % st)
         return out
 
 

@@ -192,6 +192,17 @@ _SIGS = {
                                       ctypes.c_double, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "mk_histogram_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                           ctypes.c_void_p]),
+    "mk_mlp_infer_tc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "mk_mlp_w1t_bf16": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "mk_mlp_layer1_tc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "mk_mlp_layer1_mma": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
     "mk_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mk_status_error": (ctypes.c_int, [ctypes.c_int32]),
     "mk_version": (ctypes.c_int, []),
@@ -513,6 +524,26 @@ def mlp_infer_workspace_size(batch, features, hidden):
 def mlp_infer_bf16_raw(d_params, features, hidden, d_vec, d_pa, d_pb, batch, d_logits, d_ws, ws_bytes, stream):
     _check(lib().mk_mlp_infer_bf16(d_params, features, hidden, d_vec, d_pa, d_pb, batch, d_logits, d_ws, ws_bytes,
                                    stream), "mk_mlp_infer_bf16")
+
+
+def mlp_infer_tc_raw(d_params, features, hidden, d_vec, d_pa, d_pb, batch, d_logits, d_status, d_ws, ws_bytes,
+                     stream):
+    _check(lib().mk_mlp_infer_tc(d_params, features, hidden, d_vec, d_pa, d_pb, batch, d_logits, d_status, d_ws,
+                                 ws_bytes, stream), "mk_mlp_infer_tc")
+
+
+def mlp_w1t_bf16_raw(d_params, features, hidden, d_w1t, stream):
+    _check(lib().mk_mlp_w1t_bf16(d_params, features, hidden, d_w1t, stream), "mk_mlp_w1t_bf16")
+
+
+def mlp_layer1_tc_raw(d_vec, features, d_pa, d_pb, batch, d_w1t, d_b1, d_h1, d_status, stream):
+    _check(lib().mk_mlp_layer1_tc(d_vec, features, d_pa, d_pb, batch, d_w1t, d_b1, d_h1, d_status, stream),
+           "mk_mlp_layer1_tc")
+
+
+def mlp_layer1_mma_raw(d_vec, features, d_pa, d_pb, batch, d_w1t, d_b1, d_h1, stream):
+    _check(lib().mk_mlp_layer1_mma(d_vec, features, d_pa, d_pb, batch, d_w1t, d_b1, d_h1, stream),
+           "mk_mlp_layer1_mma")
 
 
 # ------------------------------------------------------------ large frames
