@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--relations", type=int, default=1 << 18,
                     help="relations per generator and size (--workload adversarial)")
     ap.add_argument("--workload", default="census5", choices=["census5", "uneven", "separation", "learned", "adversarial", "correspondence",
-                             "atlas"],
+                             "atlas", "mlp"],
                     help="census5 (default, the headline): five-world census; uneven: 20,000 formulas "
                          "with their own class and n_max in one persistent graph-launched run; "
                          "separation: 1,024 variable-free pairs through 6 worlds exhaustively, then "
@@ -670,6 +670,73 @@ def run_atlas(args):
     print(json.dumps(out), flush=True)
 
 
+def run_mlp(args):
+    """The learned proposal's dense contraction: the MLP's first layer
+    (pairs x 8,192 0/1 features x 256 hidden, BF16, FP32 accumulation) for
+    65,536 pairs of 4,096-bit truth vectors, on tcgen05 (TMEM accumulator)
+    and on the legacy warp-level mma.sync; L2 flushed before every launch."""
+    import torch
+    from paper_2606_15437_gb300 import build as mkbuild
+    from paper_2606_15437_gb300 import engine as E
+    from paper_2606_15437_gb300 import mk
+    mkbuild.build()
+    dev = torch.device("cuda", 0)
+    F, H, B = 8192, 256, 65536
+    rng = np.random.default_rng(7)
+    vec = torch.from_numpy(rng.integers(0, 2 ** 32, size=(10000, F // 64), dtype=np.uint64)
+                           .astype(np.uint32).view(np.int32)).to(dev)
+    pa = torch.from_numpy(rng.integers(0, 10000, size=B).astype(np.int32)).to(dev)
+    pb = torch.from_numpy(rng.integers(0, 10000, size=B).astype(np.int32)).to(dev)
+    net = E.MLP(F, H, seed=3)
+    w1t = torch.empty((H, F), dtype=torch.bfloat16, device=dev)
+    sp = torch.cuda.current_stream().cuda_stream
+    mk.mlp_w1t_bf16_raw(net.params.data_ptr(), F, H, w1t.data_ptr(), sp)
+    b1 = net.params[F * H:F * H + H]
+    h1 = torch.empty((B, H), dtype=torch.float32, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def launch(impl):
+        if impl == "tc":
+            mk.mlp_layer1_tc_raw(vec.data_ptr(), F, pa.data_ptr(), pb.data_ptr(), B, w1t.data_ptr(), b1.data_ptr(),
+                                 h1.data_ptr(), st.data_ptr(), sp)
+        else:
+            mk.mlp_layer1_mma_raw(vec.data_ptr(), F, pa.data_ptr(), pb.data_ptr(), B, w1t.data_ptr(), b1.data_ptr(),
+                                  h1.data_ptr(), sp)
+
+    res = {}
+    clocks = ClockSampler(gpu_smi_id(dev, 0))
+    for impl in ("tc", "mma"):
+        for _ in range(max(3, args.warmup)):
+            launch(impl)
+        times = []
+        for _ in range(max(5, args.steps)):
+            flush.fill_(1)
+            ev = _events()
+            ev[0].record()
+            launch(impl)
+            ev[1].record()
+            torch.cuda.synchronize()
+            times.append(ev[0].elapsed_time(ev[1]))
+        res[impl] = statistics.median(times)
+    clk = clocks.stop()
+    if int(st.item()):
+        raise SystemExit("tcgen05 layer reported device status %d" % int(st.item()))
+    flops = 2.0 * B * F * H
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
+    peak = float(peaks["bf16_tflops"])
+    tc = flops / (res["tc"] / 1e3) / 1e12
+    out = {"metric": "TFLOP/s (BF16 MLP first layer)", "value": tc, "unit": "TFLOP/s", "n_gpus": 1,
+           "higher_is_better": True, "vs_baseline": None, "dtype": "bf16", "data": "synthetic (seeded)",
+           "config": {"workload": "MLP layer 1: 65,536 pairs x 8,192 features x 256 hidden", "l2": "flushed"},
+           "roofline": {"bound": "tensor", "kernel": "mlp_l1_tc_kernel", "achieved": tc, "peak": peak,
+                        "unit": "TFLOP/s", "frac": tc / peak, "peak_basis": "measured cuBLAS bf16 (burst)"},
+           "ms": res, "mma_sync_tflops": flops / (res["mma"] / 1e3) / 1e12,
+           "speedup_vs_mma_sync": res["mma"] / res["tc"], "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
 def run_profile_case(spec):
     """Small fixed launches for ncu captures (a warm-up, then the captured one)."""
     import torch
@@ -683,6 +750,26 @@ def run_profile_case(spec):
         job = E.CensusJob(W.census5_formulas()[:count], ("K",), 5, 5, samples=S, seed=SEED)
     elif kind == "separation":
         job = E.SeparateJob(W.separation_pairs(4)[:count], 6, 6, frame_lo=0, frame_hi=1 << 30)
+    elif kind == "mlp":
+        # the tcgen05 first layer on `count` pairs (full feature width), twice
+        from paper_2606_15437_gb300 import mk
+        F, H = 8192, 256
+        rng = np.random.default_rng(7)
+        vec = torch.from_numpy(rng.integers(0, 2 ** 32, size=(10000, F // 64), dtype=np.uint64)
+                               .astype(np.uint32).view(np.int32)).cuda()
+        pa = torch.from_numpy(rng.integers(0, 10000, size=count).astype(np.int32)).cuda()
+        pb = torch.from_numpy(rng.integers(0, 10000, size=count).astype(np.int32)).cuda()
+        net = E.MLP(F, H, seed=3)
+        w1t = torch.empty((H, F), dtype=torch.bfloat16, device="cuda")
+        mk.mlp_w1t_bf16_raw(net.params.data_ptr(), F, H, w1t.data_ptr(), 0)
+        h1 = torch.empty((count, H), dtype=torch.float32, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            mk.mlp_layer1_tc_raw(vec.data_ptr(), F, pa.data_ptr(), pb.data_ptr(), count, w1t.data_ptr(),
+                                 net.params[F * H:].data_ptr(), h1.data_ptr(), st.data_ptr(), 0)
+        torch.cuda.synchronize()
+        print("profile case %s done (status %d)" % (spec, int(st.item())))
+        return
     elif kind == "stress":
         # the adversarial panels' dominant shape: one-variable and constant
         # pairs on 12-world Erdos-Renyi relations, every relation and valuation
@@ -749,6 +836,8 @@ def main():
         run_correspondence(args)
     elif args.workload == "atlas":
         run_atlas(args)
+    elif args.workload == "mlp":
+        run_mlp(args)
     else:
         run_mk(args)
 
