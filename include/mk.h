@@ -414,6 +414,17 @@ int mk_mlp_layer1_tc(const uint32_t *d_vec, int32_t features, const int32_t *d_p
 int mk_mlp_layer1_mma(const uint32_t *d_vec, int32_t features, const int32_t *d_pa, const int32_t *d_pb,
                       int32_t batch, const void *d_w1t, const float *d_b1, float *d_h1, void *stream);
 
+/* The production first layer: warp-specialised (4 producer warps, 1 MMA
+   warp), 256 pairs per CTA in two M=128 accumulators (all 512 TMEM
+   columns), each W1 block fetched as one bulk copy from a pre-arranged
+   image (mk_mlp_w1_tiles: features/64 tiles of 32 KB, the swizzled K-major
+   layout the MMA reads; mk_mlp_w1_tiles_bytes gives its size). */
+size_t mk_mlp_w1_tiles_bytes(int32_t features);
+int mk_mlp_w1_tiles(const float *d_params, int32_t features, int32_t hidden, void *d_tiles, void *stream);
+int mk_mlp_layer1_tc_ws(const uint32_t *d_vec, int32_t features, const int32_t *d_pa, const int32_t *d_pb,
+                        int32_t batch, const void *d_w1_tiles, const float *d_b1, float *d_h1, int32_t *d_status,
+                        void *stream);
+
 /* ------------------------------------------- large frames (Sec. 7) */
 /* Separation beyond the exhaustive sizes runs over explicit relations on up
    to 16 worlds: the 39 stress templates (path, reverse-path, reflexive-path,

@@ -689,9 +689,10 @@ extern "C" int mk_mlp_infer_tc(const float *d_params, int32_t features, int32_t 
     cudaStream_t s = (cudaStream_t)stream;
     MlpView v = mlp_view((float *)d_params, features, hidden);
     float *h1 = (float *)d_workspace, *h2 = h1 + (size_t)batch * hidden;
-    __nv_bfloat16 *w1t = (__nv_bfloat16 *)(h2 + (size_t)batch * hidden);
-    f32_to_bf16_t_kernel<<<1024, 256, 0, s>>>(v.W1, features, hidden, w1t);
-    int rc = mk_mlp_layer1_tc(d_vec, features, d_pa, d_pb, batch, w1t, v.b1, h1, d_status, stream);
+    void *tiles = (void *)(h2 + (size_t)batch * hidden);            // features * hidden BF16, tiled
+    int rc = mk_mlp_w1_tiles(d_params, features, hidden, tiles, stream);
+    if (rc != MK_OK) return rc;
+    rc = mk_mlp_layer1_tc_ws(d_vec, features, d_pa, d_pb, batch, tiles, v.b1, h1, d_status, stream);
     if (rc != MK_OK) return rc;
     GemmArgs g;
     std::memset(&g, 0, sizeof(g));

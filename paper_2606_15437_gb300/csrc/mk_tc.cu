@@ -288,11 +288,282 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_l1_tc_kernel(TcArgs a) {
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N));
 }
 
+// --------------------------------------------------------------------------
+// Warp-specialised version: 256 pairs per CTA (two M=128 accumulators, all
+// 512 TMEM columns) share every W1 tile.  Warps 0-3 produce: each thread
+// owns two pair rows, prefetches their truth-vector words one block ahead
+// with plain loads, and writes the BF16 A rows; thread 0 also starts the
+// stage's W1 tile as ONE bulk copy (cp.async.bulk, completion counted in
+// bytes on the stage's "full" mbarrier) from a W1 image pre-arranged in
+// the swizzled tile layout (mlp_w1_tiles_kernel).  Warp 4 owns the tensor
+// memory and one elected thread issues the MMAs of a stage once its "full"
+// barrier completes, then commits to the stage's "empty" barrier.
+constexpr int WS_MT = 2;                                   // M=128 tiles per CTA
+constexpr int WS_PAIRS = WS_MT * TC_M;                      // 256 pairs
+constexpr int WS_STAGES = 3;
+constexpr int WS_PRODUCERS = 128;
+constexpr int WS_THREADS = WS_PRODUCERS + 32;
+constexpr uint32_t WS_A_BYTES = WS_MT * TC_A_BYTES;         // 32 KB
+constexpr uint32_t WS_STAGE_BYTES = WS_A_BYTES + TC_B_BYTES; // 64 KB
+constexpr uint32_t WS_SMEM_BYTES = 1024 + WS_STAGES * WS_STAGE_BYTES + 128;
+constexpr uint32_t WS_TMEM_COLS = WS_MT * TC_N;             // 512
+static_assert(WS_STAGE_BYTES % 1024 == 0, "stage tiles stay 1024-byte aligned");
+static_assert(WS_SMEM_BYTES <= 232448, "fits the 227 KB opt-in shared memory");
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Bounded wait that also gives up when the other role has aborted.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int *abort) {
+    for (uint32_t i = 0; i < TC_WAIT_SPINS; ++i) {
+        if (mbar_test(bar, parity)) return true;
+        if (*abort) return false;
+        __nanosleep(64);
+    }
+    return false;
+}
+
+// W1 (FP32 [features][256] in the parameter buffer) -> BF16 tiles: block kb
+// of 64 features is a 32 KB image of the swizzled K-major B tile, row n =
+// hidden unit n (128 bytes), 16-byte chunk c at position c ^ (n & 7).
+__global__ void mlp_w1_tiles_kernel(const float *w1, int32_t features, uint4 *tiles) {
+    const size_t nchunks = (size_t)(features / TC_KB) * TC_N * 8;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nchunks; q += (size_t)gridDim.x * blockDim.x) {
+        const int kb = (int)(q / (TC_N * 8)), rem = (int)(q % (TC_N * 8));
+        const int n = rem >> 3, c = rem & 7;
+        const int f = kb * TC_KB + c * 8;
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __nv_bfloat16 lo = __float2bfloat16(w1[(size_t)(f + 2 * i) * TC_N + n]);
+            const __nv_bfloat16 hi = __float2bfloat16(w1[(size_t)(f + 2 * i + 1) * TC_N + n]);
+            w[i] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+        }
+        tiles[(size_t)kb * (TC_B_BYTES / 16) + n * 8 + (c ^ (n & 7))] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+struct TcWsArgs {
+    const uint32_t *vec;
+    int32_t vwords;
+    const int32_t *pa, *pb;
+    int32_t batch;
+    const uint8_t *w1tiles;    // [features/64][32 KB]
+    const float *b1;
+    float *h1;
+    int32_t *status;
+};
+
+__global__ void __launch_bounds__(WS_THREADS, 1) mlp_l1_tc_ws_kernel(TcWsArgs a) {
+    extern __shared__ uint8_t tc_smem_raw[];
+    const uint32_t raw0 = smem_addr(tc_smem_raw);
+    const uint32_t pad = (1024u - (raw0 & 1023u)) & 1023u;
+    uint8_t *base = tc_smem_raw + pad;
+    const uint32_t sbase = raw0 + pad;
+    uint64_t *bars = (uint64_t *)(base + WS_STAGES * WS_STAGE_BYTES);   // full[S], empty[S], done
+    uint32_t *s_tmem = (uint32_t *)(bars + 2 * WS_STAGES + 1);
+    volatile int *s_abort = (volatile int *)(s_tmem + 1);
+    auto full = [&](int s) { return smem_addr(&bars[s]); };
+    auto empty = [&](int s) { return smem_addr(&bars[WS_STAGES + s]); };
+    const uint32_t done = smem_addr(&bars[2 * WS_STAGES]);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int p0 = blockIdx.x * WS_PAIRS;
+    const int features = a.vwords * 64, half = a.vwords * 32;
+    const int nkb = features / TC_KB;
+
+    if (tid == 0) {
+        for (int s = 0; s < WS_STAGES; ++s) {
+            mbar_init(full(s), WS_PRODUCERS);
+            mbar_init(empty(s), 1);
+        }
+        mbar_init(done, 1);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s_tmem)),
+                     "r"(WS_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *s_tmem;
+    bool ok = true;
+
+    if (warp < 4) {
+        // ---------------------------------------------------------- producers
+        const uint32_t *va[WS_MT], *vb[WS_MT];
+#pragma unroll
+        for (int m = 0; m < WS_MT; ++m) {
+            const int p = p0 + m * TC_M + tid;
+            const int ia = p < a.batch ? a.pa[p] : 0, ib = p < a.batch ? a.pb[p] : 0;
+            va[m] = a.vec + (size_t)ia * a.vwords;
+            vb[m] = a.vec + (size_t)ib * a.vwords;
+        }
+        auto fetch = [&](int kb, uint2 (&wa)[WS_MT], uint2 (&wb)[WS_MT]) {
+            const int f0 = kb * TC_KB;
+            const int w0 = (f0 < half ? f0 : f0 - half) >> 5;
+#pragma unroll
+            for (int m = 0; m < WS_MT; ++m) {
+                wa[m] = *reinterpret_cast<const uint2 *>(va[m] + w0);
+                wb[m] = *reinterpret_cast<const uint2 *>(vb[m] + w0);
+            }
+        };
+        uint2 ca[WS_MT], cb[WS_MT];
+        fetch(0, ca, cb);
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+            const int s = kb % WS_STAGES;
+            if (kb >= WS_STAGES) ok = mbar_wait_or_abort(empty(s), (uint32_t)(((kb - WS_STAGES) / WS_STAGES) & 1), s_abort);
+            if (!ok) break;
+            if (tid == 0) {
+                mbar_expect_tx(full(s), TC_B_BYTES);
+                bulk_g2s(sbase + (uint32_t)s * WS_STAGE_BYTES + WS_A_BYTES, a.w1tiles + (size_t)kb * TC_B_BYTES,
+                         TC_B_BYTES, full(s));
+            }
+            uint2 na[WS_MT], nb[WS_MT];
+            if (kb + 1 < nkb) fetch(kb + 1, na, nb);
+            const bool xr = kb * TC_KB < half;
+#pragma unroll
+            for (int m = 0; m < WS_MT; ++m) {
+                const uint32_t x0 = xr ? ca[m].x ^ cb[m].x : ca[m].x & cb[m].x;
+                const uint32_t x1 = xr ? ca[m].y ^ cb[m].y : ca[m].y & cb[m].y;
+                uint8_t *arow = base + (size_t)s * WS_STAGE_BYTES + (size_t)m * TC_A_BYTES + (size_t)tid * 128;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const uint32_t x = (c < 4 ? x0 : x1) >> ((c & 3) * 8);
+                    uint4 v;
+                    v.x = bf16_pair(x, 0);
+                    v.y = bf16_pair(x, 1);
+                    v.z = bf16_pair(x, 2);
+                    v.w = bf16_pair(x, 3);
+                    *reinterpret_cast<uint4 *>(arow + ((c ^ (tid & 7)) << 4)) = v;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(full(s));
+#pragma unroll
+            for (int m = 0; m < WS_MT; ++m) {
+                ca[m] = na[m];
+                cb[m] = nb[m];
+            }
+        }
+        if (!ok) *s_abort = 1;
+        if (ok) ok = mbar_wait_or_abort(done, 0, s_abort);
+        if (!ok) *s_abort = 1;
+    } else if (tid == WS_PRODUCERS) {
+        // --------------------------------------------------------- MMA issuer
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+            const int s = kb % WS_STAGES;
+            ok = mbar_wait_or_abort(full(s), (uint32_t)((kb / WS_STAGES) & 1), s_abort);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t st = sbase + (uint32_t)s * WS_STAGE_BYTES;
+#pragma unroll
+            for (int m = 0; m < WS_MT; ++m)
+#pragma unroll
+                for (int k = 0; k < TC_KB / 16; ++k)
+                    tc_mma(tmem + (uint32_t)(m * TC_N), sw128_desc(st + m * TC_A_BYTES + k * 32),
+                           sw128_desc(st + WS_A_BYTES + k * 32), (kb > 0 || k > 0) ? 1u : 0u);
+            tc_commit(empty(s));
+        }
+        if (ok) tc_commit(done);
+        else *s_abort = 1;
+    }
+    __syncthreads();
+    const bool aborted = *s_abort != 0;
+    if (aborted) {
+        // let bulk copies still in flight land before the CTA's memory goes
+        // (a 32 KB copy takes microseconds; this waits about 100 us)
+        if (tid == 0) {
+            atomicOr(a.status, (int)MK_ST_TIMEOUT);
+            for (int i = 0; i < 1000; ++i) __nanosleep(100);
+        }
+    } else if (warp < 4) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int lane = tid & 31;
+#pragma unroll 1
+        for (int m = 0; m < WS_MT; ++m) {
+            const int p = p0 + m * TC_M + warp * 32 + lane;      // TMEM lane = pair row of tile m
+            const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(m * TC_N);
+#pragma unroll 1
+            for (int c0 = 0; c0 < TC_N; c0 += 32) {
+                uint32_t r[32];
+                tc_ld32(trow + (uint32_t)c0, r);
+                if (p < a.batch) {
+                    float *out = a.h1 + (size_t)p * TC_N + c0;
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        float4 v;
+                        v.x = fmaxf(__uint_as_float(r[j]) + a.b1[c0 + j], 0.f);
+                        v.y = fmaxf(__uint_as_float(r[j + 1]) + a.b1[c0 + j + 1], 0.f);
+                        v.z = fmaxf(__uint_as_float(r[j + 2]) + a.b1[c0 + j + 2], 0.f);
+                        v.w = fmaxf(__uint_as_float(r[j + 3]) + a.b1[c0 + j + 3], 0.f);
+                        *reinterpret_cast<float4 *>(out + j) = v;
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 4)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(WS_TMEM_COLS));
+}
+
 }  // namespace mkd
 
 namespace {
-std::once_flag g_tc_attr;
+std::once_flag g_tc_attr, g_tc_ws_attr;
 }
+
+extern "C" size_t mk_mlp_w1_tiles_bytes(int32_t features) {
+    return features > 0 && features % 128 == 0 ? (size_t)(features / mkd::TC_KB) * mkd::TC_B_BYTES : 0;
+}
+
+extern "C" int mk_mlp_w1_tiles(const float *d_params, int32_t features, int32_t hidden, void *d_tiles, void *stream) {
+    using namespace mkd;
+    if (hidden != TC_N || features <= 0 || features % 128 || !d_params || !d_tiles || ((uintptr_t)d_tiles & 15))
+        return MK_E_ARG;
+    mlp_w1_tiles_kernel<<<1024, 256, 0, (cudaStream_t)stream>>>(d_params, features, (uint4 *)d_tiles);
+    return cudaGetLastError() == cudaSuccess ? MK_OK : MK_E_CUDA;
+}
+
+extern "C" int mk_mlp_layer1_tc_ws(const uint32_t *d_vec, int32_t features, const int32_t *d_pa, const int32_t *d_pb,
+                                   int32_t batch, const void *d_w1_tiles, const float *d_b1, float *d_h1,
+                                   int32_t *d_status, void *stream) {
+    using namespace mkd;
+    if (features <= 0 || features % 128 || batch < 0 || !d_status) return MK_E_ARG;
+    if (batch == 0) return MK_OK;
+    if (!d_vec || !d_pa || !d_pb || !d_w1_tiles || !d_b1 || !d_h1) return MK_E_ARG;
+    if (((uintptr_t)d_vec & 7) || ((uintptr_t)d_w1_tiles & 15) || ((uintptr_t)d_h1 & 15)) return MK_E_ARG;
+    std::call_once(g_tc_ws_attr, [] {
+        cudaFuncSetAttribute(mlp_l1_tc_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WS_SMEM_BYTES);
+    });
+    TcWsArgs a;
+    a.vec = d_vec;
+    a.vwords = features / 64;
+    a.pa = d_pa;
+    a.pb = d_pb;
+    a.batch = batch;
+    a.w1tiles = (const uint8_t *)d_w1_tiles;
+    a.b1 = d_b1;
+    a.h1 = d_h1;
+    a.status = d_status;
+    mlp_l1_tc_ws_kernel<<<(batch + WS_PAIRS - 1) / WS_PAIRS, WS_THREADS, WS_SMEM_BYTES, (cudaStream_t)stream>>>(a);
+    return cudaGetLastError() == cudaSuccess ? MK_OK : MK_E_CUDA;
+}
+
 
 extern "C" int mk_mlp_layer1_tc(const uint32_t *d_vec, int32_t features, const int32_t *d_pa, const int32_t *d_pb,
                                 int32_t batch, const void *d_w1t, const float *d_b1, float *d_h1, int32_t *d_status,

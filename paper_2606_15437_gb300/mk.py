@@ -203,6 +203,12 @@ _SIGS = {
     "mk_mlp_layer1_mma": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p]),
+    "mk_mlp_w1_tiles_bytes": (ctypes.c_size_t, [ctypes.c_int32]),
+    "mk_mlp_w1_tiles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "mk_mlp_layer1_tc_ws": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
     "mk_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mk_status_error": (ctypes.c_int, [ctypes.c_int32]),
     "mk_version": (ctypes.c_int, []),
@@ -539,6 +545,19 @@ def mlp_w1t_bf16_raw(d_params, features, hidden, d_w1t, stream):
 def mlp_layer1_tc_raw(d_vec, features, d_pa, d_pb, batch, d_w1t, d_b1, d_h1, d_status, stream):
     _check(lib().mk_mlp_layer1_tc(d_vec, features, d_pa, d_pb, batch, d_w1t, d_b1, d_h1, d_status, stream),
            "mk_mlp_layer1_tc")
+
+
+def mlp_w1_tiles_bytes(features):
+    return int(lib().mk_mlp_w1_tiles_bytes(int(features)))
+
+
+def mlp_w1_tiles_raw(d_params, features, hidden, d_tiles, stream):
+    _check(lib().mk_mlp_w1_tiles(d_params, features, hidden, d_tiles, stream), "mk_mlp_w1_tiles")
+
+
+def mlp_layer1_tc_ws_raw(d_vec, features, d_pa, d_pb, batch, d_tiles, d_b1, d_h1, d_status, stream):
+    _check(lib().mk_mlp_layer1_tc_ws(d_vec, features, d_pa, d_pb, batch, d_tiles, d_b1, d_h1, d_status, stream),
+           "mk_mlp_layer1_tc_ws")
 
 
 def mlp_layer1_mma_raw(d_vec, features, d_pa, d_pb, batch, d_w1t, d_b1, d_h1, stream):

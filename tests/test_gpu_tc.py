@@ -57,6 +57,11 @@ def _layer1(F, B, seed, impl):
     if impl == "tc":
         mk.mlp_layer1_tc_raw(dv.data_ptr(), F, tpa.data_ptr(), tpb.data_ptr(), B, w1t.data_ptr(), b1.data_ptr(),
                              h1.data_ptr(), st.data_ptr(), 0)
+    elif impl == "ws":
+        tiles = torch.empty(mk.mlp_w1_tiles_bytes(F), dtype=torch.uint8, device="cuda")
+        mk.mlp_w1_tiles_raw(net.params.data_ptr(), F, H, tiles.data_ptr(), 0)
+        mk.mlp_layer1_tc_ws_raw(dv.data_ptr(), F, tpa.data_ptr(), tpb.data_ptr(), B, tiles.data_ptr(), b1.data_ptr(),
+                                h1.data_ptr(), st.data_ptr(), 0)
     else:
         mk.mlp_layer1_mma_raw(dv.data_ptr(), F, tpa.data_ptr(), tpb.data_ptr(), B, w1t.data_ptr(), b1.data_ptr(),
                               h1.data_ptr(), 0)
@@ -68,9 +73,10 @@ def _layer1(F, B, seed, impl):
     return h1.cpu().numpy(), want
 
 
+@pytest.mark.parametrize("impl", ["tc", "ws"])
 @pytest.mark.parametrize("F,B", [(128, 128), (256, 1), (256, 300), (1024, 129), (8192, 700)])
-def test_layer1_tc_matches_float64(F, B):
-    got, want = _layer1(F, B, F + B, "tc")
+def test_layer1_tc_matches_float64(F, B, impl):
+    got, want = _layer1(F, B, F + B, impl)
     scale = max(1.0, float(np.abs(want).max()))
     assert np.abs(got - want).max() <= 2e-5 * scale * np.sqrt(F / 128)
 
@@ -78,8 +84,25 @@ def test_layer1_tc_matches_float64(F, B):
 def test_layer1_tc_agrees_with_mma_sync():
     a, want = _layer1(8192, 512, 11, "tc")
     b, _ = _layer1(8192, 512, 11, "mma")
+    c, _ = _layer1(8192, 512, 11, "ws")
     scale = float(np.abs(want).max())
     assert np.abs(a - b).max() <= 1e-4 * scale
+    assert np.abs(c - b).max() <= 1e-4 * scale
+
+
+def test_w1_tiles_layout():
+    F = 256
+    net = E().MLP(F, H, seed=2)
+    tiles = torch.empty(mk.mlp_w1_tiles_bytes(F), dtype=torch.uint8, device="cuda")
+    mk.mlp_w1_tiles_raw(net.params.data_ptr(), F, H, tiles.data_ptr(), 0)
+    got = tiles.cpu().numpy().view(np.uint16).reshape(F // 64, H, 64)
+    w1 = torch.from_numpy(net.params.cpu().numpy()[:F * H].reshape(F, H)).to(torch.bfloat16).view(torch.int16)
+    w1 = w1.numpy().view(np.uint16)
+    for kb in range(F // 64):
+        for n in (0, 1, 7, 8, 100, 255):
+            for c in range(8):
+                chunk = got[kb, n, 8 * (c ^ (n & 7)):8 * (c ^ (n & 7)) + 8]
+                assert np.array_equal(chunk, w1[kb * 64 + 8 * c:kb * 64 + 8 * c + 8, n])
 
 
 def test_infer_tc_matches_rounded_reference():
