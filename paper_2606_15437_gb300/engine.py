@@ -447,7 +447,7 @@ class MLP:
                            out.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(None))
         return out
 
-    def score(self, vec, pa, pb, batch=65536, impl="tc"):
+    def score(self, vec, pa, pb, batch=152 * 256 * 4, impl="tc"):
         """BF16 tensor-core logits for many pairs: first layer on tcgen05
         (mk_mlp_infer_tc), or on warp-level mma.sync (impl="mma",
         mk_mlp_infer_bf16)."""
