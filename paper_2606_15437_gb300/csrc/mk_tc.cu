@@ -290,24 +290,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_l1_tc_kernel(TcArgs a) {
 
 // --------------------------------------------------------------------------
 // Warp-specialised version: 256 pairs per CTA (two M=128 accumulators, all
-// 512 TMEM columns) share every W1 tile.  Warps 0-3 produce: each thread
-// owns two pair rows, prefetches their truth-vector words one block ahead
-// with plain loads, and writes the BF16 A rows; thread 0 also starts the
-// stage's W1 tile as ONE bulk copy (cp.async.bulk, completion counted in
-// bytes on the stage's "full" mbarrier) from a W1 image pre-arranged in
-// the swizzled tile layout (mlp_w1_tiles_kernel).  Warp 4 owns the tensor
-// memory and one elected thread issues the MMAs of a stage once its "full"
-// barrier completes, then commits to the stage's "empty" barrier.
+// 512 TMEM columns) share every W1 tile.  Three roles, decoupled by
+// mbarriers (full / empty per ring slot):
+//   - warps 0-3 produce the A tiles (a ring of WS_ASTAGES slots): each
+//     thread owns two pair rows, prefetches their truth-vector words two
+//     blocks ahead with plain loads, and writes the BF16 rows;
+//   - lane 1 of warp 4 streams the W1 tiles into a deeper ring of
+//     WS_BSTAGES slots, one bulk copy (cp.async.bulk, completion counted in
+//     bytes on the slot's "full" mbarrier) per block, from a W1 image
+//     pre-arranged in the swizzled tile layout (mlp_w1_tiles_kernel);
+//   - lane 0 of warp 4 issues the MMAs of a block once both its slots are
+//     full, then commits to both slots' "empty" barriers.
+// Warp 4 allocates and frees the tensor memory.
 constexpr int WS_MT = 2;                                   // M=128 tiles per CTA
 constexpr int WS_PAIRS = WS_MT * TC_M;                      // 256 pairs
-constexpr int WS_STAGES = 3;
+constexpr int WS_ASTAGES = 2;
+constexpr int WS_BSTAGES = 4;
 constexpr int WS_PRODUCERS = 128;
 constexpr int WS_THREADS = WS_PRODUCERS + 32;
-constexpr uint32_t WS_A_BYTES = WS_MT * TC_A_BYTES;         // 32 KB
-constexpr uint32_t WS_STAGE_BYTES = WS_A_BYTES + TC_B_BYTES; // 64 KB
-constexpr uint32_t WS_SMEM_BYTES = 1024 + WS_STAGES * WS_STAGE_BYTES + 128;
+constexpr uint32_t WS_A_BYTES = WS_MT * TC_A_BYTES;         // 32 KB per A slot
+constexpr uint32_t WS_B_OFF = WS_ASTAGES * WS_A_BYTES;      // B ring after the A ring
+constexpr uint32_t WS_RING_BYTES = WS_B_OFF + WS_BSTAGES * TC_B_BYTES;
+constexpr uint32_t WS_SMEM_BYTES = 1024 + WS_RING_BYTES + 128;
 constexpr uint32_t WS_TMEM_COLS = WS_MT * TC_N;             // 512
-static_assert(WS_STAGE_BYTES % 1024 == 0, "stage tiles stay 1024-byte aligned");
+static_assert(WS_A_BYTES % 1024 == 0 && WS_B_OFF % 1024 == 0, "tiles stay 1024-byte aligned");
 static_assert(WS_SMEM_BYTES <= 232448, "fits the 227 KB opt-in shared memory");
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
@@ -322,12 +328,12 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  : "memory");
 }
 
-// Bounded wait that also gives up when the other role has aborted.
+// Bounded wait that also gives up when another role has aborted.
 __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int *abort) {
     for (uint32_t i = 0; i < TC_WAIT_SPINS; ++i) {
         if (mbar_test(bar, parity)) return true;
         if (*abort) return false;
-        __nanosleep(64);
+        __nanosleep(32);
     }
     return false;
 }
@@ -369,12 +375,15 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mlp_l1_tc_ws_kernel(TcWsArgs a)
     const uint32_t pad = (1024u - (raw0 & 1023u)) & 1023u;
     uint8_t *base = tc_smem_raw + pad;
     const uint32_t sbase = raw0 + pad;
-    uint64_t *bars = (uint64_t *)(base + WS_STAGES * WS_STAGE_BYTES);   // full[S], empty[S], done
-    uint32_t *s_tmem = (uint32_t *)(bars + 2 * WS_STAGES + 1);
+    // barriers: fullA[A], emptyA[A], fullB[B], emptyB[B], done
+    uint64_t *bars = (uint64_t *)(base + WS_RING_BYTES);
+    uint32_t *s_tmem = (uint32_t *)(bars + 2 * WS_ASTAGES + 2 * WS_BSTAGES + 1);
     volatile int *s_abort = (volatile int *)(s_tmem + 1);
-    auto full = [&](int s) { return smem_addr(&bars[s]); };
-    auto empty = [&](int s) { return smem_addr(&bars[WS_STAGES + s]); };
-    const uint32_t done = smem_addr(&bars[2 * WS_STAGES]);
+    auto fullA = [&](int s) { return smem_addr(&bars[s]); };
+    auto emptyA = [&](int s) { return smem_addr(&bars[WS_ASTAGES + s]); };
+    auto fullB = [&](int s) { return smem_addr(&bars[2 * WS_ASTAGES + s]); };
+    auto emptyB = [&](int s) { return smem_addr(&bars[2 * WS_ASTAGES + WS_BSTAGES + s]); };
+    const uint32_t done = smem_addr(&bars[2 * WS_ASTAGES + 2 * WS_BSTAGES]);
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int p0 = blockIdx.x * WS_PAIRS;
@@ -382,9 +391,13 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mlp_l1_tc_ws_kernel(TcWsArgs a)
     const int nkb = features / TC_KB;
 
     if (tid == 0) {
-        for (int s = 0; s < WS_STAGES; ++s) {
-            mbar_init(full(s), WS_PRODUCERS);
-            mbar_init(empty(s), 1);
+        for (int s = 0; s < WS_ASTAGES; ++s) {
+            mbar_init(fullA(s), WS_PRODUCERS);
+            mbar_init(emptyA(s), 1);
+        }
+        for (int s = 0; s < WS_BSTAGES; ++s) {
+            mbar_init(fullB(s), 1);
+            mbar_init(emptyB(s), 1);
         }
         mbar_init(done, 1);
         *s_abort = 0;
@@ -400,6 +413,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mlp_l1_tc_ws_kernel(TcWsArgs a)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *s_tmem;
     bool ok = true;
+    int bulk_issued = 0;
 
     if (warp < 4) {
         // ---------------------------------------------------------- producers
@@ -420,25 +434,23 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mlp_l1_tc_ws_kernel(TcWsArgs a)
                 wb[m] = *reinterpret_cast<const uint2 *>(vb[m] + w0);
             }
         };
-        uint2 ca[WS_MT], cb[WS_MT];
+        // words of blocks kb (c*), kb+1 (n*) in registers; kb+2 requested now
+        uint2 ca[WS_MT], cb[WS_MT], na[WS_MT], nb[WS_MT];
         fetch(0, ca, cb);
+        if (nkb > 1) fetch(1, na, nb);
         for (int kb = 0; kb < nkb && ok; ++kb) {
-            const int s = kb % WS_STAGES;
-            if (kb >= WS_STAGES) ok = mbar_wait_or_abort(empty(s), (uint32_t)(((kb - WS_STAGES) / WS_STAGES) & 1), s_abort);
+            const int s = kb % WS_ASTAGES;
+            uint2 fa[WS_MT], fb[WS_MT];
+            if (kb + 2 < nkb) fetch(kb + 2, fa, fb);
+            if (kb >= WS_ASTAGES)
+                ok = mbar_wait_or_abort(emptyA(s), (uint32_t)(((kb - WS_ASTAGES) / WS_ASTAGES) & 1), s_abort);
             if (!ok) break;
-            if (tid == 0) {
-                mbar_expect_tx(full(s), TC_B_BYTES);
-                bulk_g2s(sbase + (uint32_t)s * WS_STAGE_BYTES + WS_A_BYTES, a.w1tiles + (size_t)kb * TC_B_BYTES,
-                         TC_B_BYTES, full(s));
-            }
-            uint2 na[WS_MT], nb[WS_MT];
-            if (kb + 1 < nkb) fetch(kb + 1, na, nb);
             const bool xr = kb * TC_KB < half;
 #pragma unroll
             for (int m = 0; m < WS_MT; ++m) {
                 const uint32_t x0 = xr ? ca[m].x ^ cb[m].x : ca[m].x & cb[m].x;
                 const uint32_t x1 = xr ? ca[m].y ^ cb[m].y : ca[m].y & cb[m].y;
-                uint8_t *arow = base + (size_t)s * WS_STAGE_BYTES + (size_t)m * TC_A_BYTES + (size_t)tid * 128;
+                uint8_t *arow = base + (size_t)s * WS_A_BYTES + (size_t)m * TC_A_BYTES + (size_t)tid * 128;
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const uint32_t x = (c < 4 ? x0 : x1) >> ((c & 3) * 8);
@@ -451,31 +463,49 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mlp_l1_tc_ws_kernel(TcWsArgs a)
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(full(s));
+            mbar_arrive(fullA(s));
 #pragma unroll
             for (int m = 0; m < WS_MT; ++m) {
                 ca[m] = na[m];
                 cb[m] = nb[m];
+                na[m] = fa[m];
+                nb[m] = fb[m];
             }
         }
         if (!ok) *s_abort = 1;
         if (ok) ok = mbar_wait_or_abort(done, 0, s_abort);
         if (!ok) *s_abort = 1;
+    } else if (tid == WS_PRODUCERS + 1) {
+        // ------------------------------------------------------- W1 loader
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+            const int s = kb % WS_BSTAGES;
+            if (kb >= WS_BSTAGES)
+                ok = mbar_wait_or_abort(emptyB(s), (uint32_t)(((kb - WS_BSTAGES) / WS_BSTAGES) & 1), s_abort);
+            if (!ok) break;
+            mbar_expect_tx(fullB(s), TC_B_BYTES);
+            mbar_arrive(fullB(s));
+            bulk_g2s(sbase + WS_B_OFF + (uint32_t)s * TC_B_BYTES, a.w1tiles + (size_t)kb * TC_B_BYTES, TC_B_BYTES,
+                     fullB(s));
+            ++bulk_issued;
+        }
+        if (!ok) *s_abort = 1;
     } else if (tid == WS_PRODUCERS) {
         // --------------------------------------------------------- MMA issuer
         for (int kb = 0; kb < nkb && ok; ++kb) {
-            const int s = kb % WS_STAGES;
-            ok = mbar_wait_or_abort(full(s), (uint32_t)((kb / WS_STAGES) & 1), s_abort);
+            const int sa = kb % WS_ASTAGES, sb = kb % WS_BSTAGES;
+            ok = mbar_wait_or_abort(fullB(sb), (uint32_t)((kb / WS_BSTAGES) & 1), s_abort) &&
+                 mbar_wait_or_abort(fullA(sa), (uint32_t)((kb / WS_ASTAGES) & 1), s_abort);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t st = sbase + (uint32_t)s * WS_STAGE_BYTES;
+            const uint32_t aa = sbase + (uint32_t)sa * WS_A_BYTES, bb = sbase + WS_B_OFF + (uint32_t)sb * TC_B_BYTES;
 #pragma unroll
             for (int m = 0; m < WS_MT; ++m)
 #pragma unroll
                 for (int k = 0; k < TC_KB / 16; ++k)
-                    tc_mma(tmem + (uint32_t)(m * TC_N), sw128_desc(st + m * TC_A_BYTES + k * 32),
-                           sw128_desc(st + WS_A_BYTES + k * 32), (kb > 0 || k > 0) ? 1u : 0u);
-            tc_commit(empty(s));
+                    tc_mma(tmem + (uint32_t)(m * TC_N), sw128_desc(aa + m * TC_A_BYTES + k * 32),
+                           sw128_desc(bb + k * 32), (kb > 0 || k > 0) ? 1u : 0u);
+            tc_commit(emptyA(sa));
+            tc_commit(emptyB(sb));
         }
         if (ok) tc_commit(done);
         else *s_abort = 1;
@@ -485,9 +515,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mlp_l1_tc_ws_kernel(TcWsArgs a)
     if (aborted) {
         // let bulk copies still in flight land before the CTA's memory goes
         // (a 32 KB copy takes microseconds; this waits about 100 us)
-        if (tid == 0) {
+        if (tid == WS_PRODUCERS + 1) {
             atomicOr(a.status, (int)MK_ST_TIMEOUT);
-            for (int i = 0; i < 1000; ++i) __nanosleep(100);
+            if (bulk_issued)
+                for (int i = 0; i < 1000; ++i) __nanosleep(100);
         }
     } else if (warp < 4) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
