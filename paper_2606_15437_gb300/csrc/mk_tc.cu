@@ -295,8 +295,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_l1_tc_kernel(TcArgs a) {
 //   - warps 0-3 produce the A tiles (a ring of WS_ASTAGES slots): each
 //     thread owns two pair rows, prefetches their truth-vector words two
 //     blocks ahead with plain loads, and writes the BF16 rows;
-//   - lane 1 of warp 4 streams the W1 tiles into a deeper ring of
-//     WS_BSTAGES slots, one bulk copy (cp.async.bulk, completion counted in
+//   - lane 0 of warp 5 streams the W1 tiles into a ring of
+//     WS_BSTAGES slots ahead of the MMAs, one bulk copy (cp.async.bulk, completion counted in
 //     bytes on the slot's "full" mbarrier) per block, from a W1 image
 //     pre-arranged in the swizzled tile layout (mlp_w1_tiles_kernel);
 //   - lane 0 of warp 4 issues the MMAs of a block once both its slots are
@@ -304,10 +304,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_l1_tc_kernel(TcArgs a) {
 // Warp 4 allocates and frees the tensor memory.
 constexpr int WS_MT = 2;                                   // M=128 tiles per CTA
 constexpr int WS_PAIRS = WS_MT * TC_M;                      // 256 pairs
-constexpr int WS_ASTAGES = 2;
-constexpr int WS_BSTAGES = 4;
+constexpr int WS_ASTAGES = 3;
+constexpr int WS_BSTAGES = 3;
 constexpr int WS_PRODUCERS = 128;
-constexpr int WS_THREADS = WS_PRODUCERS + 32;
+constexpr int WS_THREADS = WS_PRODUCERS + 64;             // + MMA warp + W1 loader warp
 constexpr uint32_t WS_A_BYTES = WS_MT * TC_A_BYTES;         // 32 KB per A slot
 constexpr uint32_t WS_B_OFF = WS_ASTAGES * WS_A_BYTES;      // B ring after the A ring
 constexpr uint32_t WS_RING_BYTES = WS_B_OFF + WS_BSTAGES * TC_B_BYTES;
@@ -475,8 +475,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mlp_l1_tc_ws_kernel(TcWsArgs a)
         if (!ok) *s_abort = 1;
         if (ok) ok = mbar_wait_or_abort(done, 0, s_abort);
         if (!ok) *s_abort = 1;
-    } else if (tid == WS_PRODUCERS + 1) {
-        // ------------------------------------------------------- W1 loader
+    } else if (tid == WS_PRODUCERS + 32) {
+        // ---------------------------- W1 loader (its own warp: its polling
+        // never delays the MMA issuer)
         for (int kb = 0; kb < nkb && ok; ++kb) {
             const int s = kb % WS_BSTAGES;
             if (kb >= WS_BSTAGES)
@@ -515,7 +516,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mlp_l1_tc_ws_kernel(TcWsArgs a)
     if (aborted) {
         // let bulk copies still in flight land before the CTA's memory goes
         // (a 32 KB copy takes microseconds; this waits about 100 us)
-        if (tid == WS_PRODUCERS + 1) {
+        if (tid == WS_PRODUCERS + 32) {
             atomicOr(a.status, (int)MK_ST_TIMEOUT);
             if (bulk_issued)
                 for (int i = 0; i < 1000; ++i) __nanosleep(100);
