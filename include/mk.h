@@ -82,8 +82,8 @@ extern "C" {
 /* A program is postfix code for an accumulator machine over truth sets (the
    recurrence of Thm. 1): A is the current truth set (one n-world set per
    register word lane), st[0..MK_MAX_STACK) a small stack of saved sets.
-   Instruction byte = op | operand << 4; the operand is a variable index i
-   or a stack depth d:
+   Instruction byte = op | operand << 5 (op < MK_NUM_OPS, operand < 8); the
+   operand is a variable index i or a stack depth d:
      LDV i   A = [[p_i]]            LDT  A = W              LDF  A = {}
      NOT     A = W \ A              BOX  A = {w : succ[w] subset of A}
      DIA     A = {w : succ[w] meets A}          (Lemma 1, eqs. box/dia)
@@ -92,12 +92,18 @@ extern "C" {
      IMP_S d  A = st[d] -> A      RIMP_S d  A = A -> st[d]
      AND_V i / OR_V i             A = A op [[p_i]]
      IMP_V i  A = A -> [[p_i]]    RIMP_V i  A = [[p_i]] -> A
-   A program ends with the formula's truth set in A. */
+     LDNV i  A = W \ [[p_i]]
+     AND_NV i / OR_NV i           A = A op (W \ [[p_i]])
+     IMP_NV i A = A -> (W \ [[p_i]])
+   A program ends with the formula's truth set in A.  The compiler emits
+   negation normal form (negations pushed to the atoms by De Morgan and the
+   duality of box and diamond), so NOT appears only above a biconditional. */
 enum {
     MK_OP_LDV = 0, MK_OP_LDT = 1, MK_OP_LDF = 2, MK_OP_NOT = 3, MK_OP_BOX = 4, MK_OP_DIA = 5,
     MK_OP_PUSH = 6, MK_OP_AND_S = 7, MK_OP_OR_S = 8, MK_OP_IMP_S = 9, MK_OP_RIMP_S = 10,
     MK_OP_IFF_S = 11, MK_OP_AND_V = 12, MK_OP_OR_V = 13, MK_OP_IMP_V = 14, MK_OP_RIMP_V = 15,
-    MK_NUM_OPS = 16
+    MK_OP_LDNV = 16, MK_OP_AND_NV = 17, MK_OP_OR_NV = 18, MK_OP_IMP_NV = 19,
+    MK_NUM_OPS = 20
 };
 
 typedef struct {
@@ -107,7 +113,7 @@ typedef struct {
     uint8_t modal_depth;   /* nesting depth of []/<> in the source          */
     uint8_t depth;         /* stack entries used (<= MK_MAX_STACK)          */
     uint8_t n_modal;       /* BOX/DIA instructions                          */
-    uint8_t n_bool;        /* NOT and binary instructions                   */
+    uint8_t n_bool;        /* negating and binary instructions              */
     uint8_t code[MK_MAX_CODE];
 } mk_program;              /* 104 bytes, plain data                         */
 

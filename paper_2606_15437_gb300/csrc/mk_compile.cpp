@@ -26,12 +26,13 @@ struct Node {
     Kind kind;
     int var = 0;
     int a = -1, b = -1;
+    bool neg = false;          // VAR only: the negated atom
 };
 
 struct Tree {
     std::vector<Node> nodes;
-    int add(Kind k, int a = -1, int b = -1, int var = 0) {
-        nodes.push_back(Node{k, var, a, b});
+    int add(Kind k, int a = -1, int b = -1, int var = 0, bool neg = false) {
+        nodes.push_back(Node{k, var, a, b, neg});
         return (int)nodes.size() - 1;
     }
 };
@@ -201,6 +202,43 @@ int fold(Tree &t, int id) {
     }
 }
 
+// ------------------------------------------------- negation normal form
+// Negations are pushed to the atoms (Sec. 2's clauses make each rule an
+// identity on truth sets): ~~a = a, De Morgan for & and |, ~(a -> b) =
+// a & ~b, and the duality ~[]a = <>~a, ~<>a = []~a (Lemma 1: the
+// complement of {w : succ[w] subset of t} is {w : succ[w] meets W \ t}).
+// A negated atom is a leaf of its own (the LDNV / *_NV instructions); a
+// negated biconditional keeps its NOT.  No rule adds an instruction, and
+// the tree shape (so the stack depth) is unchanged.
+int nnf(Tree &t, int id, bool neg) {
+    const Node n = t.nodes[id];
+    switch (n.kind) {
+    case TOP: return neg ? t.add(BOT) : id;
+    case BOT: return neg ? t.add(TOP) : id;
+    case VAR: return neg ? t.add(VAR, -1, -1, n.var, !n.neg) : id;
+    case NOT: return nnf(t, n.a, !neg);
+    case AND: {
+        const int a = nnf(t, n.a, neg), b = nnf(t, n.b, neg);
+        return t.add(neg ? OR : AND, a, b);
+    }
+    case OR: {
+        const int a = nnf(t, n.a, neg), b = nnf(t, n.b, neg);
+        return t.add(neg ? AND : OR, a, b);
+    }
+    case IMP: {
+        const int a = nnf(t, n.a, false), b = nnf(t, n.b, neg);
+        return t.add(neg ? AND : IMP, a, b);
+    }
+    case IFF: {
+        const int e = t.add(IFF, nnf(t, n.a, false), nnf(t, n.b, false));
+        return neg ? t.add(NOT, e) : e;
+    }
+    case BOX: return t.add(neg ? DIA : BOX, nnf(t, n.a, neg));
+    case DIA: return t.add(neg ? BOX : DIA, nnf(t, n.a, neg));
+    }
+    return id;
+}
+
 // ------------------------------------------------------------ codegen
 // Accumulator machine (mk.h): a subtree is evaluated into A; for a binary
 // node whose operands are both compound, the operand needing the deeper
@@ -237,16 +275,20 @@ struct Gen {
     }
 
     void emit(int op, int operand) {
-        code.push_back((uint8_t)(op | (operand << 4)));
+        code.push_back((uint8_t)(op | (operand << 5)));
         if (op == MK_OP_BOX || op == MK_OP_DIA) n_modal++;
-        else if (op == MK_OP_NOT || op >= MK_OP_AND_S) n_bool++;
+        else if (op == MK_OP_NOT || op >= MK_OP_AND_S) n_bool++;   // LDNV negates
     }
 
-    static int var_op(Kind k, bool var_left) {
+    // binary node with a (possibly negated) variable operand: the variable
+    // is on the left (var_left) or the right
+    static int var_op(Kind k, bool var_left, bool neg) {
         switch (k) {
-        case AND: return MK_OP_AND_V;
-        case OR: return MK_OP_OR_V;
-        default: return var_left ? MK_OP_RIMP_V : MK_OP_IMP_V;   // IMP
+        case AND: return neg ? MK_OP_AND_NV : MK_OP_AND_V;
+        case OR: return neg ? MK_OP_OR_NV : MK_OP_OR_V;
+        default:                                                    // IMP
+            if (var_left) return neg ? MK_OP_OR_V : MK_OP_RIMP_V;   // ~x -> A = x | A
+            return neg ? MK_OP_IMP_NV : MK_OP_IMP_V;
         }
     }
 
@@ -267,7 +309,7 @@ struct Gen {
         switch (n.kind) {
         case TOP: emit(MK_OP_LDT, 0); return;
         case BOT: emit(MK_OP_LDF, 0); return;
-        case VAR: emit(MK_OP_LDV, n.var); return;
+        case VAR: emit(n.neg ? MK_OP_LDNV : MK_OP_LDV, n.var); return;
         case NOT: gen(n.a, d); emit(MK_OP_NOT, 0); return;
         case BOX: gen(n.a, d); emit(MK_OP_BOX, 0); return;
         case DIA: gen(n.a, d); emit(MK_OP_DIA, 0); return;
@@ -276,7 +318,8 @@ struct Gen {
         if (fusable(n)) {
             const bool var_left = !is_var(n.b);
             gen(var_left ? n.b : n.a, d);
-            emit(var_op(n.kind, var_left), t.nodes[var_left ? n.a : n.b].var);
+            const Node &v = t.nodes[var_left ? n.a : n.b];
+            emit(var_op(n.kind, var_left, v.neg), v.var);
             return;
         }
         if (d >= MK_MAX_STACK) { overflow = true; return; }
@@ -290,7 +333,10 @@ struct Gen {
 };
 
 int compile_tree(Tree &t, int root, int nodes, int depth, int nvars, mk_program *out) {
-    int r = fold(t, root);
+    // folding can expose new negations (a -> F = ~a) and the normal form new
+    // constants (~T = F): two rounds reach the fixed point for every rule here
+    int r = fold(t, nnf(t, fold(t, root), false));
+    r = fold(t, nnf(t, r, false));
     Gen g(t);
     g.gen(r, 0);
     if (g.overflow) return MK_E_SLOTS;

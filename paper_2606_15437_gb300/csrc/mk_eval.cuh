@@ -139,7 +139,7 @@ __device__ __forceinline__ uint32_t atom_row_word(uint32_t val, int idx) {
 template <int N, int U, int BLOCK>
 __device__ __forceinline__ void decode_program(const mk_program &p, uint8_t *ops, uint16_t *offs) {
     for (int i = 0; i < p.n_instr; ++i) {
-        const int op = p.code[i] & 15, arg = p.code[i] >> 4;
+        const int op = p.code[i] & 31, arg = p.code[i] >> 5;
         ops[i] = (uint8_t)op;
         const bool stack_op = op >= MK_OP_PUSH && op <= MK_OP_IFF_S;
         offs[i] = (uint16_t)(stack_op ? arg * (U * N * BLOCK) : arg * RowShape<N>::RS);
@@ -308,6 +308,41 @@ __device__ __forceinline__ void run_program(const uint8_t *ops, const uint16_t *
                 for (int w = 0; w < N; ++w) A[u][w] = ~x[w] | A[u][w];
             }
             break;
+        case MK_OP_LDNV:
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                load_atom<N>(rw + u * ROWSTEP, A[u]);
+#pragma unroll
+                for (int w = 0; w < N; ++w) A[u][w] = ~A[u][w];
+            }
+            break;
+        case MK_OP_AND_NV:
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                uint32_t x[N];
+                load_atom<N>(rw + u * ROWSTEP, x);
+#pragma unroll
+                for (int w = 0; w < N; ++w) A[u][w] &= ~x[w];
+            }
+            break;
+        case MK_OP_OR_NV:
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                uint32_t x[N];
+                load_atom<N>(rw + u * ROWSTEP, x);
+#pragma unroll
+                for (int w = 0; w < N; ++w) A[u][w] |= ~x[w];
+            }
+            break;
+        case MK_OP_IMP_NV:
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                uint32_t x[N];
+                load_atom<N>(rw + u * ROWSTEP, x);
+#pragma unroll
+                for (int w = 0; w < N; ++w) A[u][w] = ~A[u][w] | ~x[w];
+            }
+            break;
         case MK_OP_END:
             return;
         default:
@@ -325,7 +360,8 @@ __device__ __forceinline__ bool program_ok(const mk_program &p) {
     if (p.n_instr == 0 || p.n_instr > MK_MAX_CODE || p.nvars > MK_MAX_VARS || p.depth > MK_MAX_STACK)
         return false;
     for (int i = 0; i < p.n_instr; ++i) {
-        const int op = p.code[i] & 15, arg = p.code[i] >> 4;
+        const int op = p.code[i] & 31, arg = p.code[i] >> 5;
+        if (op >= MK_NUM_OPS) return false;
         if (op == MK_OP_LDV || op >= MK_OP_AND_V) {
             if (arg >= p.nvars) return false;
         } else if (op >= MK_OP_PUSH) {

@@ -102,7 +102,7 @@ struct StressSmem {
 template <int N, int SW, int BLOCK>
 __device__ __forceinline__ void decode_ws(const mk_program &p, uint8_t *ops, uint16_t *offs) {
     for (int i = 0; i < p.n_instr; ++i) {
-        const int op = p.code[i] & 15, arg = p.code[i] >> 4;
+        const int op = p.code[i] & 31, arg = p.code[i] >> 5;
         ops[i] = (uint8_t)op;
         const bool stack_op = op >= MK_OP_PUSH && op <= MK_OP_IFF_S;
         offs[i] = (uint16_t)(stack_op ? arg * (SW * BLOCK) : arg * N);
@@ -229,6 +229,22 @@ __device__ __forceinline__ void run_ws(const uint8_t *ops, const uint16_t *offs,
         case MK_OP_RIMP_V:
 #pragma unroll
             MK_EACH A[u][w] = ~MK_ATOM(u, w) | A[u][w];
+            break;
+        case MK_OP_LDNV:
+#pragma unroll
+            MK_EACH A[u][w] = ~MK_ATOM(u, w);
+            break;
+        case MK_OP_AND_NV:
+#pragma unroll
+            MK_EACH A[u][w] &= ~MK_ATOM(u, w);
+            break;
+        case MK_OP_OR_NV:
+#pragma unroll
+            MK_EACH A[u][w] |= ~MK_ATOM(u, w);
+            break;
+        case MK_OP_IMP_NV:
+#pragma unroll
+            MK_EACH A[u][w] = ~A[u][w] | ~MK_ATOM(u, w);
             break;
         case MK_OP_END:
             return;

@@ -54,7 +54,7 @@ def run_program(prog, n, R, V):
     atom = [{w for w in range(n) if V[i][w]} for i in range(mk.MK_MAX_VARS)]
     A, st = set(), [None] * mk.MK_MAX_STACK
     for c in list(prog.code)[:prog.n_instr]:
-        op, arg = c & 15, c >> 4
+        op, arg = c & 31, c >> 5
         if op == 0:
             A = set(atom[arg])
         elif op == 1:
@@ -72,9 +72,12 @@ def run_program(prog, n, R, V):
         elif 7 <= op <= 11:
             S = st[arg]
             A = [S & A, S | A, (full - S) | A, (full - A) | S, full - (S ^ A)][op - 7]
-        else:
+        elif 12 <= op <= 15:
             a = atom[arg]
             A = [A & a, A | a, (full - A) | a, (full - a) | A][op - 12]
+        else:
+            na = full - atom[arg]
+            A = [na, A & na, A | na, (full - A) | na][op - 16]
     return A
 
 
