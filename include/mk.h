@@ -95,6 +95,8 @@ extern "C" {
      LDNV i  A = W \ [[p_i]]
      AND_NV i / OR_NV i           A = A op (W \ [[p_i]])
      IMP_NV i A = A -> (W \ [[p_i]])
+     BOX_V i / DIA_V i            A = box / dia of [[p_i]]
+     BOX_NV i / DIA_NV i          A = box / dia of W \ [[p_i]]
    A program ends with the formula's truth set in A.  The compiler emits
    negation normal form (negations pushed to the atoms by De Morgan and the
    duality of box and diamond), so NOT appears only above a biconditional. */
@@ -103,7 +105,8 @@ enum {
     MK_OP_PUSH = 6, MK_OP_AND_S = 7, MK_OP_OR_S = 8, MK_OP_IMP_S = 9, MK_OP_RIMP_S = 10,
     MK_OP_IFF_S = 11, MK_OP_AND_V = 12, MK_OP_OR_V = 13, MK_OP_IMP_V = 14, MK_OP_RIMP_V = 15,
     MK_OP_LDNV = 16, MK_OP_AND_NV = 17, MK_OP_OR_NV = 18, MK_OP_IMP_NV = 19,
-    MK_NUM_OPS = 20
+    MK_OP_BOX_V = 20, MK_OP_DIA_V = 21, MK_OP_BOX_NV = 22, MK_OP_DIA_NV = 23,
+    MK_NUM_OPS = 24
 };
 
 typedef struct {
@@ -112,7 +115,7 @@ typedef struct {
     uint8_t nvars;         /* k                                             */
     uint8_t modal_depth;   /* nesting depth of []/<> in the source          */
     uint8_t depth;         /* stack entries used (<= MK_MAX_STACK)          */
-    uint8_t n_modal;       /* BOX/DIA instructions                          */
+    uint8_t n_modal;       /* box / diamond steps                           */
     uint8_t n_bool;        /* negating and binary instructions              */
     uint8_t code[MK_MAX_CODE];
 } mk_program;              /* 104 bytes, plain data                         */

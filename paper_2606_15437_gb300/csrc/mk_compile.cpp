@@ -276,8 +276,12 @@ struct Gen {
 
     void emit(int op, int operand) {
         code.push_back((uint8_t)(op | (operand << 5)));
-        if (op == MK_OP_BOX || op == MK_OP_DIA) n_modal++;
-        else if (op == MK_OP_NOT || op >= MK_OP_AND_S) n_bool++;   // LDNV negates
+        const bool modal = op == MK_OP_BOX || op == MK_OP_DIA || op >= MK_OP_BOX_V;
+        if (modal) n_modal++;
+        // negating and binary steps (LDNV and the *_NV modal forms negate)
+        if (op == MK_OP_NOT || (op >= MK_OP_AND_S && op < MK_OP_BOX_V) || op == MK_OP_BOX_NV ||
+            op == MK_OP_DIA_NV)
+            n_bool++;
     }
 
     // binary node with a (possibly negated) variable operand: the variable
@@ -311,8 +315,17 @@ struct Gen {
         case BOT: emit(MK_OP_LDF, 0); return;
         case VAR: emit(n.neg ? MK_OP_LDNV : MK_OP_LDV, n.var); return;
         case NOT: gen(n.a, d); emit(MK_OP_NOT, 0); return;
-        case BOX: gen(n.a, d); emit(MK_OP_BOX, 0); return;
-        case DIA: gen(n.a, d); emit(MK_OP_DIA, 0); return;
+        case BOX: case DIA: {
+            const Node &c = t.nodes[n.a];
+            if (c.kind == VAR) {            // a modal step on an atom: one instruction
+                const bool box = n.kind == BOX;
+                emit(box ? (c.neg ? MK_OP_BOX_NV : MK_OP_BOX_V) : (c.neg ? MK_OP_DIA_NV : MK_OP_DIA_V), c.var);
+                return;
+            }
+            gen(n.a, d);
+            emit(n.kind == BOX ? MK_OP_BOX : MK_OP_DIA, 0);
+            return;
+        }
         default: break;
         }
         if (fusable(n)) {

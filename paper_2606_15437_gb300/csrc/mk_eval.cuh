@@ -343,6 +343,38 @@ __device__ __forceinline__ void run_program(const uint8_t *ops, const uint16_t *
                 for (int w = 0; w < N; ++w) A[u][w] = ~A[u][w] | ~x[w];
             }
             break;
+        case MK_OP_BOX_V:
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                load_atom<N>(rw + u * ROWSTEP, A[u]);
+                box_op<N>(A[u], E[NE == 1 ? 0 : u]);
+            }
+            break;
+        case MK_OP_DIA_V:
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                load_atom<N>(rw + u * ROWSTEP, A[u]);
+                dia_op<N>(A[u], E[NE == 1 ? 0 : u]);
+            }
+            break;
+        case MK_OP_BOX_NV:
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                load_atom<N>(rw + u * ROWSTEP, A[u]);
+#pragma unroll
+                for (int w = 0; w < N; ++w) A[u][w] = ~A[u][w];
+                box_op<N>(A[u], E[NE == 1 ? 0 : u]);
+            }
+            break;
+        case MK_OP_DIA_NV:
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                load_atom<N>(rw + u * ROWSTEP, A[u]);
+#pragma unroll
+                for (int w = 0; w < N; ++w) A[u][w] = ~A[u][w];
+                dia_op<N>(A[u], E[NE == 1 ? 0 : u]);
+            }
+            break;
         case MK_OP_END:
             return;
         default:

@@ -246,6 +246,17 @@ __device__ __forceinline__ void run_ws(const uint8_t *ops, const uint16_t *offs,
 #pragma unroll
             MK_EACH A[u][w] = ~A[u][w] | ~MK_ATOM(u, w);
             break;
+        case MK_OP_BOX_V:
+        case MK_OP_DIA_V:
+        case MK_OP_BOX_NV:
+        case MK_OP_DIA_NV: {
+            const uint32_t flip = (op == MK_OP_BOX_NV || op == MK_OP_DIA_NV) ? 0xFFFFFFFFu : 0u;
+#pragma unroll
+            MK_EACH A[u][w] = MK_ATOM(u, w) ^ flip;
+            if (op == MK_OP_BOX_V || op == MK_OP_BOX_NV) modal_ws<N, W, UB, V, true>(A, E, xw, xo, jw0, active);
+            else modal_ws<N, W, UB, V, false>(A, E, xw, xo, jw0, active);
+            break;
+        }
         case MK_OP_END:
             return;
         default:

@@ -75,9 +75,15 @@ def run_program(prog, n, R, V):
         elif 12 <= op <= 15:
             a = atom[arg]
             A = [A & a, A | a, (full - A) | a, (full - a) | A][op - 12]
-        else:
+        elif 16 <= op <= 19:
             na = full - atom[arg]
             A = [na, A & na, A | na, (full - A) | na][op - 16]
+        else:
+            t = atom[arg] if op in (20, 21) else full - atom[arg]
+            if op in (20, 22):
+                A = {w for w in full if succ[w] <= t}
+            else:
+                A = {w for w in full if succ[w] & t}
     return A
 
 
