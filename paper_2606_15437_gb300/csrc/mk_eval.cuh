@@ -115,8 +115,13 @@ __device__ __forceinline__ uint32_t preorder_mask(const uint32_t (&E)[N * N], bo
 // byte per instruction holding the op (MK_OP_END after the last one) and a
 // 16-bit word offset holding the operand already scaled (stack entry d ->
 // d * U*N*BLOCK, variable i -> i * RS), so dispatch is a table jump with no
-// decoding arithmetic.
+// decoding arithmetic.  A PUSH is always followed by an instruction that
+// starts a new subtree (a load, or a modal step on an atom), which does not
+// read A: the decoder folds the PUSH into it as a flag (bit 5 of the op
+// byte) and the stack entry (bits 6-7), and the interpreter saves A before
+// executing it -- one dispatch instead of two.
 
+constexpr uint32_t MK_DEC_PUSH = 32u;   // decoded op: save A to the stack first
 constexpr int MK_OP_END = MK_NUM_OPS;
 
 // Words per variable in an atom row (a multiple of 4 for 16-byte loads).
@@ -135,17 +140,30 @@ __device__ __forceinline__ uint32_t atom_row_word(uint32_t val, int idx) {
     return w < N ? 0u - ((val >> (i * N + w)) & 1u) : 0u;
 }
 
-// Decode program p into ops[0..n] (ops[n] = END) and offs[0..n).
+// An op that does not read A (the ones a PUSH can be folded into).
+__host__ __device__ __forceinline__ bool fresh_op(int op) {
+    return op == MK_OP_LDV || op == MK_OP_LDT || op == MK_OP_LDF || op == MK_OP_LDNV || op >= MK_OP_BOX_V;
+}
+
+// Decode program p into ops[0..m] (ops[m] = END, m <= n_instr) and offs[0..m).
 template <int N, int U, int BLOCK>
 __device__ __forceinline__ void decode_program(const mk_program &p, uint8_t *ops, uint16_t *offs) {
+    int j = 0;
+    uint32_t push = 0;                                  // pending PUSH folded into the next op
     for (int i = 0; i < p.n_instr; ++i) {
         const int op = p.code[i] & 31, arg = p.code[i] >> 5;
-        ops[i] = (uint8_t)op;
+        if (op == MK_OP_PUSH && !push && i + 1 < p.n_instr && fresh_op(p.code[i + 1] & 31)) {
+            push = MK_DEC_PUSH | ((uint32_t)arg << 6);
+            continue;
+        }
+        ops[j] = (uint8_t)(op | push);
+        push = 0;
         const bool stack_op = op >= MK_OP_PUSH && op <= MK_OP_IFF_S;
-        offs[i] = (uint16_t)(stack_op ? arg * (U * N * BLOCK) : arg * RowShape<N>::RS);
+        offs[j] = (uint16_t)(stack_op ? arg * (U * N * BLOCK) : arg * RowShape<N>::RS);
+        ++j;
     }
-    ops[p.n_instr] = (uint8_t)MK_OP_END;
-    offs[p.n_instr] = 0;
+    ops[j] = (uint8_t)MK_OP_END;
+    offs[j] = 0;
 }
 
 template <int N>
@@ -205,6 +223,14 @@ __device__ __forceinline__ void run_program(const uint8_t *ops, const uint16_t *
         const uint32_t op_next = ops[pc], off_next = offs[pc];
         uint32_t *st = stack + off;
         const uint32_t *rw = row0 + off;
+        if (op & MK_DEC_PUSH) {                         // folded PUSH: save A first
+            uint32_t *ps = stack + (op >> 6) * (U * N * BLOCK);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int w = 0; w < N; ++w) ps[(u * N + w) * BLOCK] = A[u][w];
+            op &= MK_DEC_PUSH - 1u;
+        }
         switch (op) {
         case MK_OP_LDV:
 #pragma unroll

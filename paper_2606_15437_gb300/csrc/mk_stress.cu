@@ -99,16 +99,26 @@ struct StressSmem {
 // Decode for the world-split interpreter: stack operands scaled to the
 // thread's stack column (d -> d*U*W*BLOCK), variable operands to the bit
 // offset of p_i in a valuation (i -> i*N).
+// A PUSH followed by an op that does not read A is folded into that op
+// (MK_DEC_PUSH flag and the stack entry in bits 6-7), as in decode_program.
 template <int N, int SW, int BLOCK>
 __device__ __forceinline__ void decode_ws(const mk_program &p, uint8_t *ops, uint16_t *offs) {
+    int j = 0;
+    uint32_t push = 0;
     for (int i = 0; i < p.n_instr; ++i) {
         const int op = p.code[i] & 31, arg = p.code[i] >> 5;
-        ops[i] = (uint8_t)op;
+        if (op == MK_OP_PUSH && !push && i + 1 < p.n_instr && fresh_op(p.code[i + 1] & 31)) {
+            push = MK_DEC_PUSH | ((uint32_t)arg << 6);
+            continue;
+        }
+        ops[j] = (uint8_t)(op | push);
+        push = 0;
         const bool stack_op = op >= MK_OP_PUSH && op <= MK_OP_IFF_S;
-        offs[i] = (uint16_t)(stack_op ? arg * (SW * BLOCK) : arg * N);
+        offs[j] = (uint16_t)(stack_op ? arg * (SW * BLOCK) : arg * N);
+        ++j;
     }
-    ops[p.n_instr] = (uint8_t)MK_OP_END;
-    offs[p.n_instr] = 0;
+    ops[j] = (uint8_t)MK_OP_END;
+    offs[j] = 0;
 }
 
 // One modal step for all U = UB*V units (unit u: block u/V): publish this
@@ -163,6 +173,14 @@ __device__ __forceinline__ void run_ws(const uint8_t *ops, const uint16_t *offs,
     for (int pc = 1;; ++pc) {
         const uint32_t op_next = ops[pc], off_next = offs[pc];
         uint32_t *st = stack + off;
+        if (op & MK_DEC_PUSH) {                         // folded PUSH: save A first
+            uint32_t *ps = stack + (op >> 6) * (U * W * BLOCK);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int w = 0; w < W; ++w) ps[(u * W + w) * BLOCK] = A[u][w];
+            op &= MK_DEC_PUSH - 1u;
+        }
         // atom truth word of p_i at world jw0+w under unit u's valuation:
         // only variable operands (off = i*N < 16) are shifts
 #define MK_ATOM(u, w) (0u - ((xs[(u) % V] >> (off + (w))) & 1u))
