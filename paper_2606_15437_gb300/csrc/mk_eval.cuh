@@ -146,13 +146,15 @@ __host__ __device__ __forceinline__ bool fresh_op(int op) {
 }
 
 // Decode program p into ops[0..m] (ops[m] = END, m <= n_instr) and offs[0..m).
-template <int N, int U, int BLOCK>
+// FOLD: fold each PUSH into the op after it (pays off when a dispatch
+// carries many units; run_program must be instantiated with the same FOLD).
+template <int N, int U, int BLOCK, bool FOLD = true>
 __device__ __forceinline__ void decode_program(const mk_program &p, uint8_t *ops, uint16_t *offs) {
     int j = 0;
     uint32_t push = 0;                                  // pending PUSH folded into the next op
     for (int i = 0; i < p.n_instr; ++i) {
         const int op = p.code[i] & 31, arg = p.code[i] >> 5;
-        if (op == MK_OP_PUSH && !push && i + 1 < p.n_instr && fresh_op(p.code[i + 1] & 31)) {
+        if (FOLD && op == MK_OP_PUSH && !push && i + 1 < p.n_instr && fresh_op(p.code[i + 1] & 31)) {
             push = MK_DEC_PUSH | ((uint32_t)arg << 6);
             continue;
         }
@@ -214,7 +216,7 @@ __device__ __forceinline__ void dia_op(uint32_t (&a)[N], const uint32_t (&E)[N *
 // Run a decoded program on U units.  Unit u's atom row is row0 + u*ROWSTEP
 // (ROWSTEP = 0: all units share one valuation); its frame word is
 // E[NE == 1 ? 0 : u]; stack: this thread's column.
-template <int N, int U, int NE, int BLOCK, int ROWSTEP>
+template <int N, int U, int NE, int BLOCK, int ROWSTEP, bool FOLD = true>
 __device__ __forceinline__ void run_program(const uint8_t *ops, const uint16_t *offs, const uint32_t *row0,
                                             const uint32_t (&E)[NE][N * N], uint32_t *stack,
                                             uint32_t (&A)[U][N]) {
@@ -223,7 +225,7 @@ __device__ __forceinline__ void run_program(const uint8_t *ops, const uint16_t *
         const uint32_t op_next = ops[pc], off_next = offs[pc];
         uint32_t *st = stack + off;
         const uint32_t *rw = row0 + off;
-        if (op & MK_DEC_PUSH) {                         // folded PUSH: save A first
+        if (FOLD && (op & MK_DEC_PUSH)) {               // folded PUSH: save A first
             uint32_t *ps = stack + (op >> 6) * (U * N * BLOCK);
 #pragma unroll
             for (int u = 0; u < U; ++u)

@@ -125,8 +125,8 @@ __global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
         s_key[i] = ~0ull;
         if (ok) {
             atomicAdd(&s_active, 1);
-            decode_program<N, U, BLOCK>(pa, s_ops_a + i * SEP_OPS_STRIDE, s_offs_a + i * SEP_OPS_STRIDE);
-            decode_program<N, U, BLOCK>(pb, s_ops_b + i * SEP_OPS_STRIDE, s_offs_b + i * SEP_OPS_STRIDE);
+            decode_program<N, U, BLOCK, false>(pa, s_ops_a + i * SEP_OPS_STRIDE, s_offs_a + i * SEP_OPS_STRIDE);
+            decode_program<N, U, BLOCK, false>(pb, s_ops_b + i * SEP_OPS_STRIDE, s_offs_b + i * SEP_OPS_STRIDE);
         }
     }
     __syncthreads();
@@ -191,8 +191,8 @@ __global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
             }
             for (uint32_t jj = 0; jj < cn && best_o > 0; ++jj) {
                 uint32_t A[U][N], B[U][N];
-                run_program<N, U, U, BLOCK, 0>(oa, fa, s_rows + jj * RW, E, s_stack, A);
-                run_program<N, U, U, BLOCK, 0>(ob, fb, s_rows + jj * RW, E, s_stack, B);
+                run_program<N, U, U, BLOCK, 0, false>(oa, fa, s_rows + jj * RW, E, s_stack, A);
+                run_program<N, U, U, BLOCK, 0, false>(ob, fb, s_rows + jj * RW, E, s_stack, B);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     uint32_t any = 0;
