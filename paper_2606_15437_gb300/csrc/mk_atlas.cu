@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(BLOCK) atlas_kernel(AtlasArgs a) {
             const uint32_t qn = min((uint32_t)AT_ROW_CAP, nq - q0);
             for (uint32_t qq = 0; qq < qn; qq += U) {
                 uint32_t A[U][N];
-                run_program<N, U, 1, BLOCK, RW, false>(ops, offs, nullptr, s_rows + qq * RW, E, s_stack, A);
+                run_program<N, U, 1, BLOCK, RW, false>(ops, offs, s_rows + qq * RW, E, s_stack, A);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const uint32_t q = q0 + qq + u;

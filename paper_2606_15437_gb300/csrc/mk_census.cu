@@ -69,8 +69,7 @@ struct TileCtx {
 // Shared memory of one CTA (tile <= MAX_TILE formulas, frames of <= NM worlds).
 template <int NM, int U, int BLOCK>
 struct TileSmem {
-    // per formula: offsets (u16), ops (u8), post-combines (u8)
-    static constexpr size_t code_bytes(int tile) { return ((size_t)tile * OPS_STRIDE * 4 + 15) & ~(size_t)15; }
+    static constexpr size_t code_bytes(int tile) { return ((size_t)tile * OPS_STRIDE * 3 + 15) & ~(size_t)15; }
     // 2 int + 3 u64 + ptr per formula, rounded up so the atom rows after it
     // stay 16-byte aligned (they are read with 16-byte loads)
     static constexpr size_t meta_bytes(int tile) { return ((size_t)tile * 40 + 15) & ~(size_t)15; }
@@ -140,7 +139,6 @@ __device__ __forceinline__ void census_tile(const TileCtx &t, uint8_t *smem) {
     const int np = t.np, cap = t.tile_cap;
     uint16_t *s_offs = (uint16_t *)smem;
     uint8_t *s_ops = smem + (size_t)cap * OPS_STRIDE * 2;
-    uint8_t *s_post = s_ops + (size_t)cap * OPS_STRIDE;
     int *s_nin = (int *)(smem + SM::code_bytes(cap));
     int *s_k = s_nin + cap;
     unsigned long long *s_cm = (unsigned long long *)(s_k + cap);
@@ -179,8 +177,7 @@ __device__ __forceinline__ void census_tile(const TileCtx &t, uint8_t *smem) {
         s_rf[i] = 0;
         s_key[i] = ~0ull;
         s_out[i] = o;
-        if (nin >= 0)
-            decode_program<N, U, BLOCK>(p, s_ops + i * OPS_STRIDE, s_offs + i * OPS_STRIDE, s_post + i * OPS_STRIDE);
+        if (nin >= 0) decode_program<N, U, BLOCK>(p, s_ops + i * OPS_STRIDE, s_offs + i * OPS_STRIDE);
     }
     __syncthreads();
     int rows_kind = -1;          // staged rows: 0 exhaustive, 1 sampled
@@ -204,7 +201,6 @@ __device__ __forceinline__ void census_tile(const TileCtx &t, uint8_t *smem) {
             const uint32_t nval = exh ? (1u << (k * N)) : t.S;
             const uint8_t *ops = s_ops + fi * OPS_STRIDE;
             const uint16_t *offs = s_offs + fi * OPS_STRIDE;
-            const uint8_t *post = s_post + fi * OPS_STRIDE;
             uint32_t cnt = 0, rf = 0, best_j = 0;
             int best_l = 32, best_w = 0;
             for (uint32_t c0 = 0; c0 < nval; c0 += ROW_CAP) {
@@ -230,7 +226,7 @@ __device__ __forceinline__ void census_tile(const TileCtx &t, uint8_t *smem) {
                         for (int u = 0; u < U; ++u) vm[u] = (jj + u < cn) ? valid : 0u;
                     }
                     uint32_t A[U][N];
-                    run_program<N, U, 1, BLOCK, RW>(ops, offs, post, s_rows + jj * RW, E, s_stack, A);
+                    run_program<N, U, 1, BLOCK, RW>(ops, offs, s_rows + jj * RW, E, s_stack, A);
                     uint32_t bad[U], any = 0;
 #pragma unroll
                     for (int u = 0; u < U; ++u) {

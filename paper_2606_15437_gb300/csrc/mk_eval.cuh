@@ -145,15 +145,11 @@ __host__ __device__ __forceinline__ bool fresh_op(int op) {
     return op == MK_OP_LDV || op == MK_OP_LDT || op == MK_OP_LDF || op == MK_OP_LDNV || op >= MK_OP_BOX_V;
 }
 
-// Decode program p into ops[0..m] (ops[m] = END, m <= n_instr), offs[0..m)
-// and, with FOLD, post[0..m].  FOLD folds each PUSH into the op after it,
-// and each stack-binary op (AND_S .. IFF_S) into the op before it as a
-// post-combine: post = 0x80 | (op - AND_S) << 2 | stack entry.  Both pay
-// off when a dispatch carries many units; run_program must be instantiated
-// with the same FOLD.
+// Decode program p into ops[0..m] (ops[m] = END, m <= n_instr) and offs[0..m).
+// FOLD: fold each PUSH into the op after it (pays off when a dispatch
+// carries many units; run_program must be instantiated with the same FOLD).
 template <int N, int U, int BLOCK, bool FOLD = true>
-__device__ __forceinline__ void decode_program(const mk_program &p, uint8_t *ops, uint16_t *offs,
-                                               uint8_t *post = nullptr) {
+__device__ __forceinline__ void decode_program(const mk_program &p, uint8_t *ops, uint16_t *offs) {
     int j = 0;
     uint32_t push = 0;                                  // pending PUSH folded into the next op
     for (int i = 0; i < p.n_instr; ++i) {
@@ -162,20 +158,14 @@ __device__ __forceinline__ void decode_program(const mk_program &p, uint8_t *ops
             push = MK_DEC_PUSH | ((uint32_t)arg << 6);
             continue;
         }
-        if (FOLD && post && j > 0 && !push && op >= MK_OP_AND_S && op <= MK_OP_IFF_S && post[j - 1] == 0) {
-            post[j - 1] = (uint8_t)(0x80u | ((uint32_t)(op - MK_OP_AND_S) << 2) | (uint32_t)arg);
-            continue;
-        }
         ops[j] = (uint8_t)(op | push);
         push = 0;
         const bool stack_op = op >= MK_OP_PUSH && op <= MK_OP_IFF_S;
         offs[j] = (uint16_t)(stack_op ? arg * (U * N * BLOCK) : arg * RowShape<N>::RS);
-        if (FOLD && post) post[j] = 0;
         ++j;
     }
     ops[j] = (uint8_t)MK_OP_END;
     offs[j] = 0;
-    if (FOLD && post) post[j] = 0;
 }
 
 template <int N>
@@ -227,12 +217,12 @@ __device__ __forceinline__ void dia_op(uint32_t (&a)[N], const uint32_t (&E)[N *
 // (ROWSTEP = 0: all units share one valuation); its frame word is
 // E[NE == 1 ? 0 : u]; stack: this thread's column.
 template <int N, int U, int NE, int BLOCK, int ROWSTEP, bool FOLD = true>
-__device__ __forceinline__ void run_program(const uint8_t *ops, const uint16_t *offs, const uint8_t *post,
-                                            const uint32_t *row0, const uint32_t (&E)[NE][N * N], uint32_t *stack,
+__device__ __forceinline__ void run_program(const uint8_t *ops, const uint16_t *offs, const uint32_t *row0,
+                                            const uint32_t (&E)[NE][N * N], uint32_t *stack,
                                             uint32_t (&A)[U][N]) {
-    uint32_t op = ops[0], off = offs[0], pst = FOLD ? post[0] : 0u;
+    uint32_t op = ops[0], off = offs[0];
     for (int pc = 1;; ++pc) {
-        const uint32_t op_next = ops[pc], off_next = offs[pc], pst_next = FOLD ? post[pc] : 0u;
+        const uint32_t op_next = ops[pc], off_next = offs[pc];
         uint32_t *st = stack + off;
         const uint32_t *rw = row0 + off;
         if (FOLD && (op & MK_DEC_PUSH)) {               // folded PUSH: save A first
@@ -418,44 +408,8 @@ __device__ __forceinline__ void run_program(const uint8_t *ops, const uint16_t *
         default:
             __builtin_unreachable();
         }
-        if (FOLD && pst) {                              // folded stack-binary op: A = st[d] op A
-            const uint32_t *cs = stack + (pst & 3u) * (U * N * BLOCK);
-            switch ((pst >> 2) & 7u) {
-            case 0:
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-#pragma unroll
-                    for (int w = 0; w < N; ++w) A[u][w] &= cs[(u * N + w) * BLOCK];
-                break;
-            case 1:
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-#pragma unroll
-                    for (int w = 0; w < N; ++w) A[u][w] |= cs[(u * N + w) * BLOCK];
-                break;
-            case 2:
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-#pragma unroll
-                    for (int w = 0; w < N; ++w) A[u][w] = ~cs[(u * N + w) * BLOCK] | A[u][w];
-                break;
-            case 3:
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-#pragma unroll
-                    for (int w = 0; w < N; ++w) A[u][w] = ~A[u][w] | cs[(u * N + w) * BLOCK];
-                break;
-            default:
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-#pragma unroll
-                    for (int w = 0; w < N; ++w) A[u][w] = ~(A[u][w] ^ cs[(u * N + w) * BLOCK]);
-                break;
-            }
-        }
         op = op_next;
         off = off_next;
-        pst = pst_next;
     }
 }
 

@@ -81,13 +81,13 @@ __global__ void __launch_bounds__(128) fingerprint_kernel(const mk_program *prog
         if (threadIdx.x == 0) {
             const mk_program &p = progs[p0 + fi];
             s_ok = program_ok(p);
-            if (s_ok) decode_program<N, 1, BLOCK, false>(p, s_ops, s_offs);
+            if (s_ok) decode_program<N, 1, BLOCK>(p, s_ops, s_offs);
             else atomicOr(status, (int)MK_ST_PROGRAM);
         }
         __syncthreads();
         if (!s_ok) continue;
         uint32_t A[1][N];
-        run_program<N, 1, 1, BLOCK, 0, false>(s_ops, s_offs, nullptr, row, E, s_stack + threadIdx.x, A);
+        run_program<N, 1, 1, BLOCK, 0>(s_ops, s_offs, row, E, s_stack + threadIdx.x, A);
         uint32_t t = 0;
 #pragma unroll
         for (int w = 0; w < N; ++w) t |= A[0][w] & wm[w];

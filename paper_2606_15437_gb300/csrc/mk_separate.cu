@@ -191,8 +191,8 @@ __global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
             }
             for (uint32_t jj = 0; jj < cn && best_o > 0; ++jj) {
                 uint32_t A[U][N], B[U][N];
-                run_program<N, U, U, BLOCK, 0, false>(oa, fa, nullptr, s_rows + jj * RW, E, s_stack, A);
-                run_program<N, U, U, BLOCK, 0, false>(ob, fb, nullptr, s_rows + jj * RW, E, s_stack, B);
+                run_program<N, U, U, BLOCK, 0, false>(oa, fa, s_rows + jj * RW, E, s_stack, A);
+                run_program<N, U, U, BLOCK, 0, false>(ob, fb, s_rows + jj * RW, E, s_stack, B);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     uint32_t any = 0;

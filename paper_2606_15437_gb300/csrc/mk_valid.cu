@@ -50,7 +50,7 @@ struct ValidArgs {
 
 template <int N, int U, int BLOCK>
 struct ValidSmem {
-    static constexpr size_t code_bytes(int tile) { return ((size_t)tile * VA_OPS_STRIDE * 4 + 15) & ~(size_t)15; }
+    static constexpr size_t code_bytes(int tile) { return ((size_t)tile * VA_OPS_STRIDE * 3 + 15) & ~(size_t)15; }
     static constexpr size_t meta_bytes(int tile) { return ((size_t)tile * 8 + 15) & ~(size_t)15; }
     static constexpr size_t row_bytes() { return (size_t)(VA_ROW_CAP + U) * RowShape<N>::WORDS * 4; }
     static constexpr size_t stack_bytes(int depth) { return (size_t)depth * U * N * BLOCK * 4; }
@@ -67,7 +67,6 @@ __global__ void __launch_bounds__(BLOCK) validity_kernel(ValidArgs a) {
     const int tile = a.tile;
     uint16_t *s_offs = (uint16_t *)smem;
     uint8_t *s_ops = smem + (size_t)tile * VA_OPS_STRIDE * 2;
-    uint8_t *s_post = s_ops + (size_t)tile * VA_OPS_STRIDE;
     int *s_nin = (int *)(smem + SM::code_bytes(tile));
     int *s_k = s_nin + tile;
     uint32_t *s_rows = (uint32_t *)(smem + SM::code_bytes(tile) + SM::meta_bytes(tile));
@@ -90,9 +89,7 @@ __global__ void __launch_bounds__(BLOCK) validity_kernel(ValidArgs a) {
         }
         s_nin[i] = nin;
         s_k[i] = p.nvars;
-        if (nin >= 0)
-            decode_program<N, U, BLOCK>(p, s_ops + i * VA_OPS_STRIDE, s_offs + i * VA_OPS_STRIDE,
-                                        s_post + i * VA_OPS_STRIDE);
+        if (nin >= 0) decode_program<N, U, BLOCK>(p, s_ops + i * VA_OPS_STRIDE, s_offs + i * VA_OPS_STRIDE);
     }
     __syncthreads();
 
@@ -115,7 +112,6 @@ __global__ void __launch_bounds__(BLOCK) validity_kernel(ValidArgs a) {
         const uint32_t nval = 1u << (s_k[fi] * N);
         const uint8_t *ops = s_ops + fi * VA_OPS_STRIDE;
         const uint16_t *offs = s_offs + fi * VA_OPS_STRIDE;
-        const uint8_t *post = s_post + fi * VA_OPS_STRIDE;
         uint32_t rf = 0;                                    // lanes refuted so far
         for (uint32_t c0 = 0; c0 < nval; c0 += VA_ROW_CAP) {
             // uniform: every thread takes the same staging decisions; the
@@ -132,7 +128,7 @@ __global__ void __launch_bounds__(BLOCK) validity_kernel(ValidArgs a) {
             if (rf != valid) {
                 for (uint32_t jj = 0; jj < cn; jj += U) {
                     uint32_t A[U][N];
-                    run_program<N, U, 1, BLOCK, RW>(ops, offs, post, s_rows + jj * RW, E, s_stack, A);
+                    run_program<N, U, 1, BLOCK, RW>(ops, offs, s_rows + jj * RW, E, s_stack, A);
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
                         uint32_t all = A[u][0];
