@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "mk.h"
+#include "mk_attr.h"
 #include "mk_eval.cuh"
 
 namespace mkd {
@@ -363,22 +364,12 @@ namespace {
 
 using namespace mkd;
 
-std::mutex g_at_mutex;
-std::vector<const void *> g_at_attr;
 
 template <int N>
 void launch_atlas(const AtlasArgs &a, cudaStream_t s) {
     using SM = AtlasSmem<N, AT_U, AT_BLOCK>;
     auto kern = atlas_kernel<N, AT_U, AT_BLOCK>;
-    {
-        std::lock_guard<std::mutex> lock(g_at_mutex);
-        bool done = false;
-        for (auto p : g_at_attr) done |= p == (const void *)kern;
-        if (!done) {
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::total());
-            g_at_attr.push_back((const void *)kern);
-        }
-    }
+    ensure_dynamic_smem((const void *)kern, SM::total());
     dim3 grid((unsigned)((a.nframes + AT_BLOCK - 1) / AT_BLOCK), (unsigned)((a.nprog + AT_TILE - 1) / AT_TILE));
     kern<<<grid, AT_BLOCK, SM::total(), s>>>(a);
 }
@@ -436,11 +427,7 @@ extern "C" int mk_power_iteration(const double *d_gram, int32_t F, const double 
     if (F < 1 || F > MK_MAX_ATLAS_AXIS || nprev < 0 || iters < 1 || !d_gram || !d_v || !d_lambda || (nprev && !d_prev))
         return MK_E_ARG;
     const size_t sm = 2 * (size_t)F * sizeof(double);
-    static std::once_flag once;
-    std::call_once(once, [] {
-        cudaFuncSetAttribute(power_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(2 * MK_MAX_ATLAS_AXIS * sizeof(double)));
-    });
+    ensure_dynamic_smem((const void *)power_kernel, 2 * MK_MAX_ATLAS_AXIS * sizeof(double));
     power_kernel<<<1, 1024, sm, (cudaStream_t)stream>>>(d_gram, F, d_prev, nprev, iters, d_v, d_lambda);
     return cudaGetLastError() == cudaSuccess ? MK_OK : MK_E_CUDA;
 }

@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "mk.h"
+#include "mk_attr.h"
 #include "mk_eval.cuh"
 
 namespace mkd {
@@ -565,23 +566,10 @@ int check_cfg(const mk_census_cfg *cfg, int32_t nprog) {
 // Dynamic shared memory above 48 KB needs a per-kernel attribute; it is
 // raised when a kernel first needs more (so a call made once before a
 // stream capture leaves nothing to set during the capture).
-std::mutex g_attr_mutex;
-std::vector<std::pair<const void *, size_t>> g_attr_done;
 
 template <typename K>
 void ensure_smem(K kern, size_t bytes) {
-    std::lock_guard<std::mutex> lock(g_attr_mutex);
-    const void *key = (const void *)kern;
-    for (auto &e : g_attr_done)
-        if (e.first == key) {
-            if (bytes > e.second) {
-                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-                e.second = bytes;
-            }
-            return;
-        }
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    g_attr_done.push_back({key, bytes});
+    ensure_dynamic_smem((const void *)kern, bytes);
 }
 
 template <int N, int U, int BLOCK>

@@ -27,6 +27,7 @@
 #include <cstring>
 
 #include "mk.h"
+#include "mk_attr.h"
 #include "mk_eval.cuh"
 
 namespace mkd {
@@ -497,7 +498,7 @@ extern "C" int mk_hamming_knn(const uint32_t *d_bits, int32_t nvec, int32_t word
     if (!d_workspace || ws_bytes < mk_knn_workspace_size(nvec)) return MK_E_WORKSPACE;
     const size_t sm = ((size_t)words * 32 + 1 + words) * 4;
     if (sm > 200 * 1024) return MK_E_ARG;
-    cudaFuncSetAttribute(knn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    ensure_dynamic_smem((const void *)knn_kernel, sm);
     knn_kernel<<<nvec, 512, sm, (cudaStream_t)stream>>>(d_bits, nvec, words, k, d_nbr, d_dist,
                                                         (uint16_t *)d_workspace);
     return cudaGetLastError() == cudaSuccess ? MK_OK : MK_E_CUDA;

@@ -21,6 +21,7 @@
 #include <cstring>
 
 #include "mk.h"
+#include "mk_attr.h"
 #include "mk_eval.cuh"
 
 namespace mkd {
@@ -257,7 +258,7 @@ void launch_sep(const SepArgs &a, cudaStream_t s) {
     dim3 grid((unsigned)((words + per_cta - 1) / per_cta), (unsigned)((a.npairs + a.tile - 1) / a.tile));
     const size_t sm = SepSmem<N, U, SEP_BLOCK>::total(a.tile);
     auto kern = separate_kernel<N, U, SEP_BLOCK>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    ensure_dynamic_smem((const void *)kern, sm);
     kern<<<grid, SEP_BLOCK, sm, s>>>(a);
 }
 

@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "mk.h"
+#include "mk_attr.h"
 #include "mk_eval.cuh"
 #include "mk_relgen.cuh"
 
@@ -486,17 +487,10 @@ namespace {
 
 using namespace mkd;
 
-std::mutex g_st_mutex;
-std::vector<const void *> g_st_attr;
-
 template <typename K>
 void st_smem(K kern, size_t bytes) {
-    std::lock_guard<std::mutex> lock(g_st_mutex);
-    for (auto p : g_st_attr)
-        if (p == (const void *)kern) return;
     // every launch of one instantiation asks for at most the tile-64 size
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    g_st_attr.push_back((const void *)kern);
+    ensure_dynamic_smem((const void *)kern, bytes);
 }
 
 template <int N, int W, int UB, int V>

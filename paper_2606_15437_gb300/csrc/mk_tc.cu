@@ -31,6 +31,7 @@
 #include <mutex>
 
 #include "mk.h"
+#include "mk_attr.h"
 
 namespace mkd {
 
@@ -555,9 +556,6 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mlp_l1_tc_ws_kernel(TcWsArgs a)
 
 }  // namespace mkd
 
-namespace {
-std::once_flag g_tc_attr, g_tc_ws_attr;
-}
 
 extern "C" size_t mk_mlp_w1_tiles_bytes(int32_t features) {
     return features > 0 && features % 128 == 0 ? (size_t)(features / mkd::TC_KB) * mkd::TC_B_BYTES : 0;
@@ -579,9 +577,7 @@ extern "C" int mk_mlp_layer1_tc_ws(const uint32_t *d_vec, int32_t features, cons
     if (batch == 0) return MK_OK;
     if (!d_vec || !d_pa || !d_pb || !d_w1_tiles || !d_b1 || !d_h1) return MK_E_ARG;
     if (((uintptr_t)d_vec & 7) || ((uintptr_t)d_w1_tiles & 15) || ((uintptr_t)d_h1 & 15)) return MK_E_ARG;
-    std::call_once(g_tc_ws_attr, [] {
-        cudaFuncSetAttribute(mlp_l1_tc_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WS_SMEM_BYTES);
-    });
+    ensure_dynamic_smem((const void *)mlp_l1_tc_ws_kernel, WS_SMEM_BYTES);
     TcWsArgs a;
     a.vec = d_vec;
     a.vwords = features / 64;
@@ -608,9 +604,7 @@ extern "C" int mk_mlp_layer1_tc(const uint32_t *d_vec, int32_t features, const i
     if (!d_vec || !d_pa || !d_pb || !d_w1t || !d_b1 || !d_h1) return MK_E_ARG;
     // 8- and 16-byte copies: truth-vector rows and W1^T rows must stay aligned
     if (((uintptr_t)d_vec & 7) || ((uintptr_t)d_w1t & 15) || ((uintptr_t)d_h1 & 15)) return MK_E_ARG;
-    std::call_once(g_tc_attr, [] {
-        cudaFuncSetAttribute(mlp_l1_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BYTES);
-    });
+    ensure_dynamic_smem((const void *)mlp_l1_tc_kernel, TC_SMEM_BYTES);
     TcArgs a;
     a.vec = d_vec;
     a.vwords = features / 64;

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "mk.h"
+#include "mk_attr.h"
 #include "mk_eval.cuh"
 
 namespace mkd {
@@ -274,22 +275,9 @@ namespace {
 
 using namespace mkd;
 
-std::mutex g_va_mutex;
-std::vector<std::pair<const void *, size_t>> g_va_attr;
-
 template <typename K>
 void va_smem(K kern, size_t bytes) {
-    std::lock_guard<std::mutex> lock(g_va_mutex);
-    for (auto &e : g_va_attr)
-        if (e.first == (const void *)kern) {
-            if (bytes > e.second) {
-                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-                e.second = bytes;
-            }
-            return;
-        }
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    g_va_attr.push_back({(const void *)kern, bytes});
+    ensure_dynamic_smem((const void *)kern, bytes);
 }
 
 template <int N>
