@@ -18,8 +18,9 @@
  *     kernel, an iteration limit reached) are OR-ed as MK_ST_* bits into the
  *     caller's int32 device word d_status (clear it before the call);
  *     mk_status_error() maps a read-back status to an MK_E_* code.
- *   - Calls on distinct buffers and streams are thread-safe: the library has
- *     no global state.
+ *   - Calls on distinct buffers and streams are thread-safe.  The library's
+ *     only global state is a mutex-guarded cache of the kernel attributes it
+ *     has set on each device (and the fixed scratch of mk_census_noalloc).
  *
  * Encodings (the readings of the paper behind them are listed in the design doc)
  *   - World w of an n-world frame is bit w of a mask; full = 2^n - 1 (Sec. 3).
