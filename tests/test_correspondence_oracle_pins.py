@@ -7,6 +7,7 @@ from math import comb
 import numpy as np
 import pytest
 
+import golden_fixtures as G
 import oracle
 from oracle import pyref
 
@@ -61,13 +62,13 @@ def test_inclusions_between_conditions():
         assert np.array_equal(c["symmetric"] & c["transitive"], c["symmetric"] & c["Euclidean"])
 
 
-TABLE9 = [("[]p -> p", "reflexive"), ("[]p -> <>p", "serial"), ("[]p -> [][]p", "transitive"),
-          ("<>p -> []<>p", "Euclidean"), ("p -> []<>p", "symmetric"), ("<>p -> []p", "partially functional"),
-          ("[][]p -> []p", "dense"), ("<>[]p -> []<>p", "directed")]
+# Table 9's landmarks and its McKinsey control, from tests/golden
+TABLE9 = [(f, c) for _, f, c in G.table9() if c is not None]
+MCKINSEY = [f for _, f, c in G.table9() if c is None][0]
 
 
 @pytest.mark.parametrize("N", (3, 4))
 def test_table9_recovery(N):
     for text, cond in TABLE9:
         assert cond in oracle.recover(text, N), (text, cond)
-    assert oracle.recover("[]<>p -> <>[]p", N) == []          # McKinsey: no match in the library
+    assert oracle.recover(MCKINSEY, N) == []          # McKinsey: no match in the library

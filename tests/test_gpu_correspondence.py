@@ -7,6 +7,7 @@ import random
 import numpy as np
 import pytest
 
+import golden_fixtures as G
 import oracle
 from paper_2606_15437_gb300 import build as mkbuild
 from paper_2606_15437_gb300 import mk
@@ -105,13 +106,13 @@ def test_mismatch_counts():
             assert got[i, j] == sum(bin(int(w)).count("1") for w in x)
 
 
-TABLE9 = [("[]p -> p", "reflexive"), ("[]p -> <>p", "serial"), ("[]p -> [][]p", "transitive"),
-          ("<>p -> []<>p", "Euclidean"), ("p -> []<>p", "symmetric"), ("<>p -> []p", "partially functional"),
-          ("[][]p -> []p", "dense"), ("<>[]p -> []<>p", "directed")]
+# Table 9's landmarks and its McKinsey control, from tests/golden
+TABLE9 = [(f, c) for _, f, c in G.table9() if c is not None]
+MCKINSEY = [f for _, f, c in G.table9() if c is None][0]
 
 
 def test_table9_recovery_and_confirmation():
-    texts = [t for t, _ in TABLE9] + ["[]<>p -> <>[]p", "([]p -> p) & ([]p -> [][]p)", "p | ~p", "p"]
+    texts = [t for t, _ in TABLE9] + [MCKINSEY, "([]p -> p) & ([]p -> [][]p)", "p | ~p", "p"]
     rows, stats = E().recover_correspondents(texts, N=4, confirm_n=5)
     for (t, cond), r in zip(TABLE9, rows):
         assert cond in r["matches"] and r["confirmed"], (t, r)

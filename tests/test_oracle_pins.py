@@ -13,6 +13,7 @@ import random
 import numpy as np
 import pytest
 
+import golden_fixtures as G
 import oracle
 from oracle import pyref
 from paper_2606_15437_gb300 import workloads as W
@@ -180,10 +181,12 @@ def _conds(n):
     }
 
 
-CORRESPONDENCES = [("[]p -> p", "reflexive"), ("[]p -> <>p", "serial"), ("[]p -> [][]p", "transitive"),
-          ("<>p -> []<>p", "euclidean"), ("p -> []<>p", "symmetric"),
-          ("<>p -> []p", "partial_function"), ("[][]p -> []p", "dense"),
-          ("<>[]p -> []<>p", "confluent")]
+# Table 9's landmarks (tests/golden), with this file's names for the conditions
+_NAMES = {"reflexive": "reflexive", "serial": "serial", "transitive": "transitive", "Euclidean": "euclidean",
+          "symmetric": "symmetric", "partially functional": "partial_function", "dense": "dense",
+          "directed": "confluent"}
+CORRESPONDENCES = [(f, _NAMES[c]) for _, f, c in G.table9() if c is not None]
+MCKINSEY = [f for _, f, c in G.table9() if c is None]
 
 
 @pytest.mark.parametrize("axiom,cond", CORRESPONDENCES)
@@ -197,7 +200,8 @@ def test_correspondence(axiom, cond, n):
 
 def test_mckinsey_matches_no_library_condition():
     n = 3
-    valid = oracle.frame_valid_all("[]<>p -> <>[]p", n)
+    assert MCKINSEY == ["[]<>p -> <>[]p"]
+    valid = oracle.frame_valid_all(MCKINSEY[0], n)
     for name, c in _conds(n).items():
         want = np.array([c(f) for f in range(2 ** (n * n))], np.uint8)
         assert not np.array_equal(valid, want), name
@@ -207,9 +211,11 @@ def test_mckinsey_matches_no_library_condition():
 
 def test_alpha1_alpha2_first_split_at_four():
     # Table 3: m = 1 is UNSAT through 3 worlds, first SAT at 4
-    for n in (1, 2, 3):
+    m, through, first = G.table3()[0]
+    assert (m, through, first) == (1, 3, 4)
+    for n in range(1, through + 1):
         assert oracle.pair_layer(alpha(1), alpha(2), n)["split"] is None
-    r = oracle.pair_layer(alpha(1), alpha(2), 4)
+    r = oracle.pair_layer(alpha(1), alpha(2), first)
     f, v, w, a, b = r["split"]
     # the brute-force second path agrees on the first split
     assert pyref.first_split(alpha(1), alpha(2), 4) == (f, v, w)
@@ -220,7 +226,9 @@ def test_alpha1_alpha2_first_split_at_four():
 @pytest.mark.slow
 def test_alpha2_alpha3_agree_through_five_split_at_six():
     # Prop. 5: agreement on every frame of at most five worlds ...
-    for n in (1, 2, 3, 4, 5):
+    m, through, first = G.table3()[1]
+    assert (m, through, first) == (2, 5, 6)
+    for n in range(1, through + 1):
         assert oracle.pair_layer(alpha(2), alpha(3), n)["split"] is None
     # ... and a split at six worlds; the first one in K-index order:
     r = oracle.pair_layer(alpha(2), alpha(3), 6, f_lo=0, f_hi=17335329)
@@ -232,15 +240,28 @@ def test_alpha2_alpha3_agree_through_five_split_at_six():
     assert [pyref.sat(R, {}, 2, t) for t in tr] == [True, False]
 
 
+def _nodes(tree):
+    return 1 + sum(_nodes(c) for c in tree[1:] if isinstance(c, tuple))
+
+
 def test_paper_certificate_alpha2_alpha3_path():
     # Prop. 5: successor masks (2,4,8,16,32,0), falsifying world w0
-    succ = [2, 4, 8, 16, 32, 0]
-    n = 6
+    cert = G.keyed("prop5_alpha_path_certificate.txt")
+    phi, psi = cert["phi"], cert["psi"]
+    assert (phi, psi) == (alpha(2), alpha(3))
+    # Prop. 5 gives the formulas five and seven nodes
+    assert (_nodes(pyref.parse(phi)), _nodes(pyref.parse(psi))) == (int(cert["phi_nodes"]), int(cert["psi_nodes"]))
+    succ = [int(x) for x in cert["succ"].split()]
+    w0 = int(cert["world"])
+    n = len(succ)
     R = np.array([[(succ[w] >> v) & 1 for v in range(n)] for w in range(n)], np.uint8)
     f = sum(((succ[w] >> v) & 1) << (w * n + v) for w in range(n) for v in range(n))
     assert f == 541098242
-    assert oracle.eval_model(alpha(2), R)[0] == 1
-    assert oracle.eval_model(alpha(3), R)[0] == 0
+    assert oracle.eval_model(phi, R)[w0] == 1
+    assert oracle.eval_model(psi, R)[w0] == 0
+    # the pure-Python path agrees
+    Rs = {(x, y) for x in range(n) for y in range(n) if R[x, y]}
+    assert [pyref.sat(Rs, {}, w0, pyref.parse(t)) for t in (phi, psi)] == [True, False]
 
 
 @pytest.mark.parametrize("m", [1, 2, 3, 4, 5])
@@ -265,9 +286,30 @@ def test_lemma8_path_family(m):
 
 
 def test_alpha3_alpha4_agree_through_four():
-    # Table 3: m = 3 is UNSAT through 7 worlds (exhaustive check to 4 here)
+    # Table 3: m = 3 is UNSAT through 7 worlds (exhaustive check to 4 here),
+    # first SAT at 8 worlds: the 8-world path of Lemma 2 separates them
+    m, through, first = G.table3()[2]
+    assert (m, through, first) == (3, 7, 8)
     for n in (1, 2, 3, 4):
         assert oracle.pair_layer(alpha(3), alpha(4), n)["split"] is None
+    R = np.zeros((first, first), np.uint8)
+    for w in range(first - 1):
+        R[w, w + 1] = 1
+    assert (oracle.eval_model(alpha(3), R)[0], oracle.eval_model(alpha(4), R)[0]) == (1, 0)
+
+
+def test_table1_matched_workload_size():
+    # Table 1: 262,144 five-world frames x all valuations of p, q = 268,435,456
+    # cases; the formula is a K theorem, so no prefix of frames refutes it
+    wl = G.keyed("table1_matched_workload.txt")
+    r = oracle.census(wl["formula"], "K", int(wl["worlds"]), f_lo=0, f_hi=64)
+    assert r["nvals"] == int(wl["valuations"])
+    assert int(wl["frames"]) * r["nvals"] == int(wl["cases"])
+    assert (r["cm_count"], r["frames_refuted"], r["witness"]) == (0, 0, None)
+    # the bench's matched row is this workload
+    row = W.matched_rows()[0]
+    assert (row["text"], row["frames"], row["valuations"], row["hi"]) == \
+        (wl["formula"], int(wl["frames"]), int(wl["valuations"]), int(wl["frames"]))
 
 
 # ------------------------------------------------------ brute force (pyref)
