@@ -149,9 +149,17 @@ typedef struct {
     uint8_t max_depth;         /* largest program depth in the batch (0 = the    */
                                /* limit MK_MAX_STACK); sizes the device stack;   */
                                /* a deeper program sets MK_ST_PROGRAM            */
-    uint8_t reserved;
+    uint8_t max_vars;          /* largest variable count in the batch (0 =       */
+                               /* unknown); only caps the valuation split below  */
     uint32_t samples;          /* S (0 = always exhaustive)                      */
-    uint32_t reserved2;
+    uint32_t vsplit;           /* valuation chunks per layer, <= 4096: 0 = auto  */
+                               /* (split a layer whose grid of frame words x     */
+                               /* formula tiles is under 1,216 CTAs, four waves  */
+                               /* of 2 CTAs on 152 SMs), 1 = never, v > 1 = v    */
+                               /* chunks on every layer.  Only the default tune  */
+                               /* (units 8, block 256) splits.  Results are the  */
+                               /* same either way; a split layer needs the       */
+                               /* workspace's frame-word bitmap (below)          */
     const uint32_t *d_samples; /* device [(n_max+1) * S]: row n = layer n's S    */
                                /* sampled valuations; NULL iff S == 0            */
     uint64_t frame_lo;         /* only frames with K index in [frame_lo,         */
@@ -167,7 +175,12 @@ typedef struct {
                                /* sample slot); UINT64_MAX = no countermodel     */
 } mk_result;
 
-/* Workspace bytes mk_census needs for this configuration and batch. */
+/* Workspace bytes mk_census needs for this configuration and batch: the
+   S4/S5 frame lists and, when some layer splits its valuations, a bitmap of
+   nprog x (that layer's frame words) u32 words in which the chunks OR their
+   refuted frames, plus one u32 counter per formula tile (the last CTA of a
+   tile to finish counts the bitmap).  Given less (but at least the lists'
+   share), mk_census runs every layer unsplit. */
 size_t mk_census_workspace_size(const mk_census_cfg *cfg, int32_t nprog);
 
 /* Census (Alg. 1 over every selected (class, n) layer, Thm. 2): for each
@@ -188,9 +201,10 @@ int mk_census(const mk_program *d_progs, int32_t nprog, const mk_census_cfg *cfg
    is a packaging of mk_census.  Arguments and results are those of
    mk_census; the scratch space is a fixed array of MK_NOALLOC_SCRATCH_BYTES
    inside the library, held on every GPU that loads it until the process
-   exits.  Configurations whose mk_census_workspace_size exceeds that limit
-   (S4 or S5 at n = 6) are rejected with MK_E_WORKSPACE before anything is
-   launched.  The first call on a device looks up the array's address
+   exits.  Configurations whose S4/S5 frame lists exceed that limit (S4 or
+   S5 at n = 6) are rejected with MK_E_WORKSPACE before anything is
+   launched; layers split their valuations only when the split bitmap also
+   fits (mk_census_workspace_size <= the limit).  The first call on a device looks up the array's address
    (cudaGetSymbolAddress) with that device current; make that first call
    before any stream capture.  All calls share the one array, and it keeps
    the last call's contents: every part of it that a call reads is written

@@ -44,6 +44,31 @@ constexpr int SRC_K = 0, SRC_T = 1, SRC_LIST = 2;
 constexpr int ROW_CAP = 128;                   // atom rows staged at a time
 constexpr int OPS_STRIDE = MK_MAX_CODE + 2;   // decoded ops per program (END + prefetch pad)
 constexpr int MAX_TILE = 64;
+constexpr int VCHUNK = 32;                     // valuation-split granularity (whole units)
+
+// Valuation groups of a CTA (see census_tile): a split layer's CTA with
+// fewer frame words than BLOCK / 2 also shares its valuations among G groups
+// of nwr threads (nwr = its words rounded up to a power of two).
+__host__ __device__ inline int vgroups(uint64_t nw, int block, int units, int *nwr_out) {
+    int nwr = block;
+    while (nwr > 1 && (uint64_t)(nwr / 2) >= nw) nwr /= 2;
+    if (nwr_out) *nwr_out = nwr;
+    const int g = block / nwr, cap = ROW_CAP / units;
+    return g < cap ? g : cap;
+}
+
+// The split kernel variant is built for the default tune only (U = 8,
+// BLOCK = 256); layers of other tunes are never split.
+template <int U, int BLOCK>
+constexpr bool kSplitTune = U == 8 && BLOCK == 256;
+
+// Chunk granularity of a split CTA: whole passes of its G groups, at least
+// VCHUNK valuations, so each thread has several units to amortise its
+// program staging.
+__host__ __device__ inline uint64_t vgran(int G, int units) {
+    const uint64_t g = (uint64_t)G * units;
+    return g > (uint64_t)VCHUNK ? g : (uint64_t)VCHUNK;
+}
 
 // One tile: where its formulas, frames and outputs are.
 struct TileCtx {
@@ -65,6 +90,14 @@ struct TileCtx {
     int32_t tile_cap;          // formulas the shared-memory layout holds
     int32_t report;            // 1: this CTA reports program errors
     int32_t *status;
+};
+
+// A split layer (valuations shared out over grid.z): kept apart from TileCtx
+// so the unsplit kernels see exactly the context they always had.
+struct SplitCtx {
+    uint32_t vsplit, vpart;    // valuation chunks of the layer; this CTA's chunk
+    uint32_t *rf_bits;         // OR of refuted lanes per (formula, word)
+    uint64_t rf_w0, rf_words;  //   the layer's first word and its words per formula
 };
 
 // Shared memory of one CTA (tile <= MAX_TILE formulas, frames of <= NM worlds).
@@ -133,8 +166,8 @@ __device__ __forceinline__ void stage_rows(uint32_t *s_rows, bool exh, const uin
 
 // The census of one tile on n = N worlds.  All threads of the CTA call it
 // with the same t; smem is laid out by TileSmem<NM, U, BLOCK> with NM >= N.
-template <int N, int NM, int U, int BLOCK>
-__device__ __forceinline__ void census_tile(const TileCtx &t, uint8_t *smem) {
+template <int N, int NM, int U, int BLOCK, bool SPLIT = false>
+__device__ __forceinline__ void census_tile(const TileCtx &t, uint8_t *smem, const SplitCtx &sp = SplitCtx()) {
     using SM = TileSmem<NM, U, BLOCK>;
     constexpr int RW = RowShape<N>::WORDS;
     const int np = t.np, cap = t.tile_cap;
@@ -184,9 +217,21 @@ __device__ __forceinline__ void census_tile(const TileCtx &t, uint8_t *smem) {
     int rows_kind = -1;          // staged rows: 0 exhaustive, 1 sampled
     uint32_t rows_c0 = 0;
     const int lane = threadIdx.x & 31;
+    // A split layer's CTA with few frame words (a tiny window under many
+    // valuations) also shares each staged block of valuations among its
+    // threads: G groups of nwr threads (nwr = words rounded up to a power of
+    // two), group g taking units g, g + G, ... of the block.  Threads with the
+    // same word then OR their refuted lanes into the split bitmap and take
+    // the CTA's least witness key by an atomic min.
+    // (all of the split -- chunks, groups, the bitmap -- is a compile-time
+    // variant, so the kernels of unsplit layers carry none of it)
+    int nwr = BLOCK, G = 1;
+    if constexpr (SPLIT) G = vgroups(t.w1 - t.w0, BLOCK, U, &nwr);
+    const uint32_t sub = SPLIT ? (uint32_t)(threadIdx.x / nwr) : 0u;
+    const uint64_t gran = vgran(G, U);
 
     for (uint64_t wg = t.w0; wg < t.w1; wg += BLOCK) {
-        const uint64_t word = wg + threadIdx.x;
+        const uint64_t word = wg + (SPLIT ? (threadIdx.x & (nwr - 1)) : threadIdx.x);
         uint32_t E[1][N * N];
         uint32_t valid = 0;
         if (word < t.w1) valid = build_word<N>(t, word, E[0]);
@@ -200,12 +245,21 @@ __device__ __forceinline__ void census_tile(const TileCtx &t, uint8_t *smem) {
             const int k = s_k[fi];
             const bool exh = exhaustive_vals(k, N, t.S);
             const uint32_t nval = exh ? (1u << (k * N)) : t.S;
+            // this CTA's chunk of the valuations, a multiple of its granule
+            // (whole passes of its groups); rows are staged from its start
+            uint32_t v_lo = 0, v_hi = nval;
+            if constexpr (SPLIT) {
+                const uint64_t per = ((nval + (uint64_t)sp.vsplit - 1) / sp.vsplit + gran - 1) / gran * gran;
+                v_lo = (uint32_t)min((uint64_t)nval, (uint64_t)sp.vpart * per);
+                v_hi = (uint32_t)min((uint64_t)nval, (uint64_t)v_lo + per);
+                if (v_lo >= v_hi) continue;
+            }
             const uint8_t *ops = s_ops + fi * OPS_STRIDE;
             const uint16_t *offs = s_offs + fi * OPS_STRIDE;
             uint32_t cnt = 0, rf = 0, best_j = 0;
             int best_l = 32, best_w = 0;
-            for (uint32_t c0 = 0; c0 < nval; c0 += ROW_CAP) {
-                const uint32_t cn = min((uint32_t)ROW_CAP, nval - c0);
+            for (uint32_t c0 = v_lo; c0 < v_hi; c0 += ROW_CAP) {
+                const uint32_t cn = min((uint32_t)ROW_CAP, v_hi - c0);
                 // uniform across the CTA: every thread takes the same decisions.
                 // Exhaustive rows are staged ROW_CAP at a time, sampled ones up to S.
                 if (rows_kind != (exh ? 0 : 1) || rows_c0 != c0) {
@@ -221,7 +275,7 @@ __device__ __forceinline__ void census_tile(const TileCtx &t, uint8_t *smem) {
                 uint32_t vm[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) vm[u] = valid;
-                for (uint32_t jj = 0; jj < cn; jj += U) {
+                for (uint32_t jj = SPLIT ? sub * U : 0u; jj < cn; jj += SPLIT ? (uint32_t)G * U : (uint32_t)U) {
                     if (jj + U > cn) {
 #pragma unroll
                         for (int u = 0; u < U; ++u) vm[u] = (jj + u < cn) ? valid : 0u;
@@ -264,8 +318,18 @@ __device__ __forceinline__ void census_tile(const TileCtx &t, uint8_t *smem) {
             // warp reduction: counts split in 16-bit halves so the sums fit
             const uint32_t c_hi = __reduce_add_sync(0xFFFFFFFFu, cnt >> 16);
             const uint32_t c_lo = __reduce_add_sync(0xFFFFFFFFu, cnt & 0xFFFFu);
-            const uint32_t f_sum = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(rf));
-            const uint32_t hit = __ballot_sync(0xFFFFFFFFu, best_l < 32);
+            // frames refuted: a popcount, unless other CTAs hold other valuations
+            // of the same frames; then the frame words are ORed and counted later
+            uint32_t f_sum = 0;
+            if constexpr (SPLIT) {
+                if (rf) atomicOr(&sp.rf_bits[(size_t)(t.p0 + fi) * sp.rf_words + (word - sp.rf_w0)], rf);
+            } else {
+                f_sum = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(rf));
+            }
+            if (SPLIT && G > 1 && best_l < 32)
+                atomicMin(&s_key[fi], (unsigned long long)((lane_kindex<N>(t, word, best_l) << 27) |
+                                                           ((uint64_t)best_j << 3) | (uint64_t)best_w));
+            const uint32_t hit = (SPLIT && G > 1) ? 0u : __ballot_sync(0xFFFFFFFFu, best_l < 32);
             uint64_t key = ~0ull;
             if (hit) {
                 // lanes hold ascending frames, so the lowest hit lane has the least frame
@@ -299,9 +363,47 @@ struct LayerArgs {
     TileCtx t;                 // w0/w1: the layer's word range; p0/np unused
     int32_t tile;
     const uint64_t *list_len;  // SRC_LIST: device count
+    SplitCtx sp;               // split layers: vsplit > 1
+    uint32_t *rf_done;         //   and their CTAs finished, per formula tile
 };
 
-template <int N, int U, int BLOCK>
+// The end of a split layer's CTA: the last CTA of its formula tile to finish
+// (counted on rf_done, the pattern of a threadfence reduction) counts the
+// tile's ORed frame words into frames_refuted, then clears the words and the
+// counter for the next split layer.  Nothing waits: the other CTAs just exit.
+template <int BLOCK>
+__device__ void split_layer_tail(const LayerArgs &a, const TileCtx &t, const SplitCtx &sp) {
+    __shared__ int s_last;
+    __shared__ unsigned long long s_sum;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned total = gridDim.x * gridDim.z;
+        s_last = atomicAdd(&a.rf_done[blockIdx.y], 1u) == total - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int i = 0; i < t.np; ++i) {
+        uint32_t *b = sp.rf_bits + (size_t)(t.p0 + i) * sp.rf_words;
+        if (threadIdx.x == 0) s_sum = 0;
+        __syncthreads();
+        uint32_t sum = 0;
+        for (uint64_t w = threadIdx.x; w < sp.rf_words; w += BLOCK) {
+            sum += __popc(__ldcg(b + w));
+            b[w] = 0;
+        }
+        sum = __reduce_add_sync(0xFFFFFFFFu, sum);
+        if ((threadIdx.x & 31) == 0 && sum) atomicAdd(&s_sum, (unsigned long long)sum);
+        __syncthreads();
+        if (threadIdx.x == 0)
+            t.out[(size_t)(t.p0 + i) * t.out_stride + t.out_off].frames_refuted = s_sum;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a.rf_done[blockIdx.y] = 0;
+}
+
+template <int N, int U, int BLOCK, bool SPLIT>
 __global__ void __launch_bounds__(BLOCK) census_layer_kernel(LayerArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     TileCtx t = a.t;
@@ -309,21 +411,32 @@ __global__ void __launch_bounds__(BLOCK) census_layer_kernel(LayerArgs a) {
     t.np = min(a.tile, t.np - t.p0);
     t.w0 = a.t.w0 + (uint64_t)blockIdx.x * BLOCK;
     t.w1 = min(t.w0 + BLOCK, a.t.w1);
-    t.report = blockIdx.x == 0;
+    t.report = blockIdx.x == 0 && (!SPLIT || blockIdx.z == 0);
     t.tile_cap = a.tile;
     if (t.src == SRC_LIST) {
         const uint64_t len = *a.list_len;
         t.nframes = len < t.nframes ? len : t.nframes;
     }
-    census_tile<N, N, U, BLOCK>(t, smem);
+    if constexpr (SPLIT) {
+        SplitCtx sp = a.sp;
+        sp.vpart = blockIdx.z;
+        census_tile<N, N, U, BLOCK, true>(t, smem, sp);
+        split_layer_tail<BLOCK>(a, t, sp);
+    } else {
+        census_tile<N, N, U, BLOCK>(t, smem);
+    }
 }
 
-__global__ void init_results_kernel(mk_result *out, size_t n) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+// Clears the results and, when some layer splits its valuations, the frame
+// bitmap and the per-tile CTA counters that follow it.
+__global__ void init_results_kernel(mk_result *out, size_t n, uint32_t *clear, size_t nclear) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
         out[i].cm_count = 0;
         out[i].frames_refuted = 0;
         out[i].witness_key = ~0ull;
     }
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nclear; i += stride) clear[i] = 0;
 }
 
 // ------------------------------------------------- persistent work queue
@@ -512,6 +625,74 @@ uint64_t layer_frames(int cls, int n) {
     }
 }
 
+// Number of T frames (compact indices) whose K index is below x: t_to_k is
+// monotone, so a binary search over compact indices.
+uint64_t t_rank(uint64_t x, int n) {
+    uint64_t lo = 0, hi = t_frames(n);
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (t_to_k(mid, n) < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Frame words [w0, w1) a layer scans: K frames of the window by index, T
+// frames of the window by compact index (a contiguous range, since t_to_k is
+// monotone), S4/S5 lists whole (their lanes are filtered by K index).
+void layer_words(const mk_census_cfg *cfg, int c, int n, uint64_t *w0, uint64_t *w1) {
+    uint64_t lo, hi;
+    if (c == 0) {
+        const uint64_t kf = 1ull << (n * n);
+        lo = cfg->frame_lo;
+        hi = cfg->frame_hi < kf ? cfg->frame_hi : kf;
+    } else if (c == 1) {
+        lo = t_rank(cfg->frame_lo, n);
+        hi = t_rank(cfg->frame_hi, n);
+    } else {
+        lo = 0;
+        hi = layer_frames(c, n);
+    }
+    *w0 = lo / 32;
+    *w1 = lo >= hi ? *w0 : (hi + 31) / 32;
+}
+
+// Valuation chunks of a layer.  A layer whose grid (frame words x formula
+// tiles) is too small to keep the GPU busy -- few formulas on few frames
+// with many valuations each, the underfilled shapes of Table 4 -- also
+// splits the valuations over grid.z, up to kFillCtas CTAs: four waves of
+// census_layer_kernel's two resident CTAs on each of a GB300's 152 SMs (so
+// the last wave's tail costs at most a quarter).
+constexpr uint64_t kFillCtas = 4ull * 2 * 152;
+constexpr uint32_t kMaxVsplit = 4096;
+
+uint32_t layer_vsplit(const mk_census_cfg *cfg, int n, uint64_t words, int32_t nprog) {
+    const int block = cfg->tune.block ? cfg->tune.block : 256;
+    const int units = cfg->tune.units ? cfg->tune.units : 8;
+    if (words == 0 || nprog == 0 || cfg->vsplit == 1 || units != 8 || block != 256) return 1;
+    if (cfg->vsplit > 1) return cfg->vsplit;
+    const uint64_t tile = cfg->tune.tile ? cfg->tune.tile : 16;
+    const uint64_t wpc = words < (uint64_t)block ? words : (uint64_t)block;   // words of a CTA
+    const int G = vgroups(wpc, block, units, nullptr);
+    const uint64_t ctas = ((words + block - 1) / block) * ((nprog + tile - 1) / tile);
+    if (ctas >= kFillCtas) return 1;
+    uint64_t v = (kFillCtas + ctas - 1) / ctas;
+    if (v > kMaxVsplit) v = kMaxVsplit;
+    if (cfg->max_vars) {
+        // no more chunks than the batch's largest valuation set has granules
+        uint64_t nval = 1;
+        for (int k = 0; k <= cfg->max_vars && k <= MK_MAX_VARS; ++k) {
+            const uint64_t m = exhaustive_vals(k, n, cfg->samples) ? (k * n < 64 ? 1ull << (k * n) : ~0ull)
+                                                                   : cfg->samples;
+            if (m > nval) nval = m;
+        }
+        const uint64_t gran = vgran(G, units);
+        const uint64_t blocks = (nval + gran - 1) / gran;
+        if (v > blocks) v = blocks;
+    }
+    return (uint32_t)(v > 1 ? v : 1);
+}
+
 struct ListPlan {
     size_t list_off[2][7];   // [S4, S5][n]: byte offset of the list
     size_t len_off[2][7];    // device count
@@ -549,12 +730,51 @@ ListPlan plan_lists(uint32_t classes, int n_min, int n_max) {
     return p;
 }
 
+// Lists plus, after them, the frame-word bitmap that split layers OR their
+// refuted lanes into (one region, reused layer after layer).
+struct CensusPlan {
+    ListPlan lists;
+    size_t rf_off, rf_bytes;   // frame bitmap of the largest split layer
+    size_t done_off;           // then one CTA counter per formula tile
+    size_t clear_words;        // bitmap + counters, cleared at the start
+    size_t total;
+};
+
+CensusPlan plan_census(const mk_census_cfg *cfg, int32_t nprog) {
+    CensusPlan p;
+    p.lists = plan_lists(cfg->classes, cfg->n_min, cfg->n_max);
+    p.rf_off = align256(p.lists.total);
+    p.rf_bytes = 0;
+    for (int c = 0; c < 4; ++c) {
+        if (!(cfg->classes & (1u << c))) continue;
+        for (int n = cfg->n_min; n <= cfg->n_max; ++n) {
+            uint64_t w0, w1;
+            layer_words(cfg, c, n, &w0, &w1);
+            if (layer_vsplit(cfg, n, w1 - w0, nprog) > 1) {
+                const size_t b = (size_t)nprog * (w1 - w0) * 4;
+                if (b > p.rf_bytes) p.rf_bytes = b;
+            }
+        }
+    }
+    const uint64_t tile = cfg->tune.tile ? cfg->tune.tile : 16;
+    p.done_off = p.rf_off + p.rf_bytes;
+    p.clear_words = 0;
+    p.total = p.lists.total;
+    if (p.rf_bytes) {
+        const size_t done_bytes = (size_t)((nprog + tile - 1) / tile) * 4;
+        p.clear_words = (p.rf_bytes + done_bytes) / 4;
+        p.total = align256(p.done_off + done_bytes);
+    }
+    return p;
+}
+
 int check_cfg(const mk_census_cfg *cfg, int32_t nprog) {
     if (!cfg || nprog < 0) return MK_E_ARG;
     if ((cfg->classes & 15u) == 0 || (cfg->classes & ~15u)) return MK_E_ARG;
     if (cfg->n_min < 1 || cfg->n_max > MK_MAX_WORLDS_EXH || cfg->n_min > cfg->n_max) return MK_E_ARG;
     if ((cfg->samples == 0) != (cfg->d_samples == nullptr)) return MK_E_ARG;
     if (cfg->frame_lo > cfg->frame_hi) return MK_E_ARG;
+    if (cfg->vsplit > 4096) return MK_E_ARG;
     const mk_tune &t = cfg->tune;
     if (t.block && t.block != 128 && t.block != 256) return MK_E_ARG;
     if (t.tile > MAX_TILE) return MK_E_ARG;
@@ -576,9 +796,13 @@ template <int N, int U, int BLOCK>
 void launch_layer_b(const LayerArgs &a, cudaStream_t s) {
     const uint64_t words = a.t.w1 > a.t.w0 ? a.t.w1 - a.t.w0 : 0;
     if (words == 0 || a.t.np == 0) return;
-    dim3 grid((unsigned)((words + BLOCK - 1) / BLOCK), (unsigned)((a.t.np + a.tile - 1) / a.tile));
+    dim3 grid((unsigned)((words + BLOCK - 1) / BLOCK), (unsigned)((a.t.np + a.tile - 1) / a.tile),
+              a.sp.vsplit);
     const size_t sm = TileSmem<N, U, BLOCK>::total(a.tile, a.t.depth);
-    auto kern = census_layer_kernel<N, U, BLOCK>;
+    // split layers (default tune only) take the split variant
+    auto kern = census_layer_kernel<N, U, BLOCK, false>;
+    if constexpr (kSplitTune<U, BLOCK>)
+        if (a.sp.vsplit > 1) kern = census_layer_kernel<N, U, BLOCK, true>;
     ensure_smem(kern, sm);
     kern<<<grid, BLOCK, sm, s>>>(a);
 }
@@ -632,10 +856,11 @@ void launch_list_n(int n, uint8_t *ws, const ListPlan &p, int c, int32_t *status
     }
 }
 
-void launch_init(mk_result *out, size_t n, cudaStream_t s) {
-    if (!n) return;
-    const size_t blocks = (n + 255) / 256;
-    init_results_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(out, n);
+void launch_init(mk_result *out, size_t n, cudaStream_t s, uint32_t *clear = nullptr, size_t nclear = 0) {
+    const size_t m = n > nclear ? n : nclear;
+    if (!m) return;
+    const size_t blocks = (m + 255) / 256;
+    init_results_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(out, n, clear, nclear);
 }
 
 }  // namespace
@@ -660,17 +885,22 @@ extern "C" int32_t mk_census_launches(const mk_census_cfg *cfg, int32_t nprog) {
     for (int c = 0; c < 4; ++c)
         if (cfg->classes & (1u << c))
             for (int n = cfg->n_min; n <= cfg->n_max; ++n) {
-                if (c == 0) {
-                    const uint64_t kf = 1ull << (n * n);
-                    const uint64_t hi = cfg->frame_hi < kf ? cfg->frame_hi : kf;
-                    if (cfg->frame_lo >= hi) continue;
-                }
+                uint64_t w0, w1;
+                layer_words(cfg, c, n, &w0, &w1);
+                if (w1 == w0) continue;
                 ++layers;
             }
     return 1 + lists * nn * 3 + layers;
 }
 
 extern "C" size_t mk_census_workspace_size(const mk_census_cfg *cfg, int32_t nprog) {
+    if (check_cfg(cfg, nprog) != MK_OK) return 0;
+    return plan_census(cfg, nprog).total;
+}
+
+// The least workspace mk_census accepts: the frame lists alone.  With less
+// than mk_census_workspace_size it runs every layer unsplit.
+size_t mk_census_min_workspace(const mk_census_cfg *cfg, int32_t nprog) {
     if (check_cfg(cfg, nprog) != MK_OK) return 0;
     return plan_lists(cfg->classes, cfg->n_min, cfg->n_max).total;
 }
@@ -682,14 +912,17 @@ extern "C" int mk_census(const mk_program *d_progs, int32_t nprog, const mk_cens
     if (rc != MK_OK) return rc;
     if (nprog > 0 && (!d_progs || !d_out)) return MK_E_ARG;
     if (!d_status) return MK_E_ARG;
-    const ListPlan plan = plan_lists(cfg->classes, cfg->n_min, cfg->n_max);
+    const CensusPlan cplan = plan_census(cfg, nprog);
+    const ListPlan &plan = cplan.lists;
     if (!d_workspace || ws_bytes < plan.total) return MK_E_WORKSPACE;
+    const bool may_split = ws_bytes >= cplan.total;
     cudaStream_t s = (cudaStream_t)stream;
     uint8_t *ws = (uint8_t *)d_workspace;
 
     const int ncls = class_count(cfg->classes);
     const int nn = cfg->n_max - cfg->n_min + 1;
-    launch_init(d_out, (size_t)nprog * ncls * nn, s);
+    launch_init(d_out, (size_t)nprog * ncls * nn, s, may_split ? (uint32_t *)(ws + cplan.rf_off) : nullptr,
+                may_split ? cplan.clear_words : 0);
 
     const int block = cfg->tune.block ? cfg->tune.block : 256;
     const int tile = cfg->tune.tile ? cfg->tune.tile : 16;
@@ -725,25 +958,27 @@ extern "C" int mk_census(const mk_program *d_progs, int32_t nprog, const mk_cens
             t.out_off = ci * nn + (n - cfg->n_min);
             t.depth = depth;
             t.status = d_status;
+            layer_words(cfg, c, n, &t.w0, &t.w1);
             if (c == 0) {
                 t.src = SRC_K;
                 t.nframes = kframes;
-                const uint64_t hi = cfg->frame_hi < kframes ? cfg->frame_hi : kframes;
-                t.w0 = cfg->frame_lo / 32;
-                t.w1 = cfg->frame_lo >= hi ? t.w0 : (hi + 31) / 32;
             } else if (c == 1) {
                 t.src = SRC_T;
                 t.nframes = t_frames(n);
-                t.w0 = 0;
-                t.w1 = (t.nframes + 31) / 32;
             } else {
                 const int li = c - 2;
                 t.src = SRC_LIST;
                 t.flist = (const uint64_t *)(ws + plan.list_off[li][n]);
                 a.list_len = (const uint64_t *)(ws + plan.len_off[li][n]);
                 t.nframes = li == 0 ? kPreorders[n] : kEquivalences[n];
-                t.w0 = 0;
-                t.w1 = (t.nframes + 31) / 32;
+            }
+            if (t.w1 == t.w0) continue;
+            a.sp.vsplit = may_split ? layer_vsplit(cfg, n, t.w1 - t.w0, nprog) : 1;
+            if (a.sp.vsplit > 1) {
+                a.sp.rf_bits = (uint32_t *)(ws + cplan.rf_off);
+                a.sp.rf_w0 = t.w0;
+                a.sp.rf_words = t.w1 - t.w0;
+                a.rf_done = (uint32_t *)(ws + cplan.done_off);
             }
             launch_layer_n(n, a, block, units, s);
         }

@@ -34,7 +34,7 @@ __device__ __forceinline__ uint32_t bit_word(uint64_t x, int b) {
 // K index of the reflexive frame with compact index c: the n diagonal edge
 // bits are inserted as ones, the off-diagonal bits taken from c in order
 // (monotone, so compact order is K order).
-__device__ __forceinline__ uint64_t t_to_k(uint64_t c, int n) {
+__host__ __device__ __forceinline__ uint64_t t_to_k(uint64_t c, int n) {
     uint64_t f = 0;
     int j = 0;
     for (int e = 0; e < n * n; ++e) {

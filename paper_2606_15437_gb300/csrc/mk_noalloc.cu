@@ -49,9 +49,13 @@ int scratch_address(void **out) {
 
 }  // namespace
 
+// mk_census.cu: the frame lists' share of the workspace (the least that
+// mk_census accepts; with it alone every layer runs unsplit).
+size_t mk_census_min_workspace(const mk_census_cfg *cfg, int32_t nprog);
+
 extern "C" int mk_census_noalloc(const mk_program *d_progs, int32_t nprog, const mk_census_cfg *cfg,
                                  mk_result *d_out, int32_t *d_status, void *stream) {
-    const size_t need = mk_census_workspace_size(cfg, nprog);
+    const size_t need = mk_census_min_workspace(cfg, nprog);
     if (need == 0) return MK_E_ARG;
     if (need > MK_NOALLOC_SCRATCH_BYTES) return MK_E_WORKSPACE;
     void *scratch = nullptr;

@@ -30,7 +30,7 @@ class CensusJob:
 
     def __init__(self, texts=None, classes=CLASSES, n_min=1, n_max=5, samples=256, seed=2,
                  device="cuda", tune=None, frame_lo=0, frame_hi=mk.NO_KEY, progs=None,
-                 sample_table=None):
+                 sample_table=None, vsplit=0):
         if not torch.cuda.is_available():
             raise RuntimeError("CensusJob needs a CUDA device (there is no CPU fallback)")
         self.texts = list(texts) if texts is not None else None
@@ -51,7 +51,8 @@ class CensusJob:
         depth = int(self.progs["depth"].max()) if self.nprog else 0
         self.cfg = mk.census_cfg(self.classes, n_min, n_max, samples,
                                  self.d_samples.data_ptr() if samples else 0, frame_lo, frame_hi, tune,
-                                 max_depth=max(depth, 1))
+                                 max_depth=max(depth, 1), vsplit=vsplit,
+                                 max_vars=int(self.progs["nvars"].max()) if self.nprog else 0)
         self.ws_bytes = mk.census_workspace_size(self.cfg, self.nprog)
         if self.ws_bytes == 0:
             raise mk.MkError(-5, "mk_census_workspace_size")

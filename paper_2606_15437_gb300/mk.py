@@ -43,8 +43,8 @@ class mk_tune(ctypes.Structure):
 
 class mk_census_cfg(ctypes.Structure):
     _fields_ = [("classes", ctypes.c_uint32), ("n_min", ctypes.c_uint8), ("n_max", ctypes.c_uint8),
-                ("max_depth", ctypes.c_uint8), ("reserved", ctypes.c_uint8), ("samples", ctypes.c_uint32),
-                ("reserved2", ctypes.c_uint32), ("d_samples", ctypes.c_void_p),
+                ("max_depth", ctypes.c_uint8), ("max_vars", ctypes.c_uint8), ("samples", ctypes.c_uint32),
+                ("vsplit", ctypes.c_uint32), ("d_samples", ctypes.c_void_p),
                 ("frame_lo", ctypes.c_uint64), ("frame_hi", ctypes.c_uint64), ("tune", mk_tune)]
 
 
@@ -289,9 +289,11 @@ def class_mask(classes):
 
 
 def census_cfg(classes, n_min, n_max, samples=0, d_samples=0, frame_lo=0, frame_hi=NO_KEY, tune=None,
-               max_depth=0):
+               max_depth=0, vsplit=0, max_vars=0):
     cfg = mk_census_cfg()
     cfg.max_depth = max_depth
+    cfg.max_vars = max_vars
+    cfg.vsplit = vsplit
     cfg.classes = class_mask(classes) if not isinstance(classes, int) else classes
     cfg.n_min, cfg.n_max = n_min, n_max
     cfg.samples = samples

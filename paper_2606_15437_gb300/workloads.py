@@ -380,3 +380,61 @@ def pointed_models(seed=5, counts=(32, 96, 640, 1280, 2048)):
             out.append((frame, val, n, world, 0))
         groups += [n] * (cnt // 32)
     return np.array(out, dtype=dtype), np.array(groups, np.int32)
+
+
+# ------------------------------------------- matched single-formula shapes
+
+def t_frame_kindex(c, n):
+    """K index of the reflexive n-world frame with compact index c (the
+    diagonal bits set, the off-diagonal bits taken from c in order)."""
+    f, j = 0, 0
+    for e in range(n * n):
+        if e % (n + 1) == 0:
+            f |= 1 << e
+        else:
+            f |= ((c >> j) & 1) << e
+            j += 1
+    return f
+
+
+_CHAIN3 = "[](p0 -> p1) & [](p1 -> p2) -> ([]p0 -> []p2)"
+_CHAIN4 = "[](p0 -> p1) & [](p1 -> p2) & [](p2 -> p3) -> ([]p0 -> []p3)"
+
+
+def matched_rows():
+    """Single-formula workloads on five-world frames with every valuation:
+    Table 1's matched case and the shapes of Table 4's ablation (frames x
+    valuations per row), plus the three-variable depth-ten stress of Sec. 8
+    (34.36 G evaluations: 2^20 frames x 2^15 valuations).  The paper names
+    the formula of Table 1 only; the others are chosen here to have the
+    row's operator count, modal depth or variable count.  Frames are a
+    prefix in K-index order (T: the first compact indices).  'h100' is the
+    paper's measured rate for the row in G evaluations/s, for context.
+
+    Returns dicts: name, text, cls, lo, hi (K-index window), frames,
+    valuations, h100."""
+    K = "K"
+    rows = [
+        ("Table 1: matched formula", "[](p -> q) -> (<>p -> <>q)", K, 262144, 1024, 38.33),
+        ("Table 4: length 2 ops", "[]p -> p", K, 65536, 32, 14.87),
+        ("Table 4: length 5 ops", "[](p -> <>p) -> []p", K, 65536, 32, 11.88),
+        ("Table 4: length 11 ops", "[](p -> <>p) -> (<>[]p -> [](<>p | ~p))", K, 65536, 32, 5.50),
+        ("Table 4: modal depth 1", "<>p -> []p", K, 65536, 32, 7.45),
+        ("Table 4: modal depth 4", "[]<>[]<>p -> p", K, 65536, 32, 6.89),
+        ("Table 4: modal depth 8", "[]<>[]<>[]<>[]<>p -> p", K, 65536, 32, 11.56),
+        ("Table 4: 1 variable", "[](p0 -> <>p0) -> <>p0", K, 65536, 32, 15.72),
+        ("Table 4: 2 variables", "[](p0 -> p1) -> ([]p0 -> []p1)", K, 8192, 1024, 7.15),
+        ("Table 4: 3 variables, underfilled", _CHAIN3, K, 512, 32768, 0.400),
+        ("Table 4: 3 variables, saturated", _CHAIN3, K, 8192, 32768, 6.38),
+        ("Table 4: 4 variables, underfilled", _CHAIN4, K, 32, 1048576, 0.0207),
+        ("Table 4: frame filter K", "[]p -> [][]p", K, 65536, 32, 7.21),
+        ("Table 4: frame filter T", "[]p -> [][]p", "T", 2049, 32, 0.240),
+        ("Sec. 8: semantic stress (3 vars, depth 10)", "[]<>[]<>[]<>[]<>[]<>(p0 & p1 -> p2) -> <>p0",
+         K, 1 << 20, 32768, 24.08),
+    ]
+    out = []
+    for name, text, cls, frames, vals, h100 in rows:
+        hi = frames if cls == K else t_frame_kindex(frames, 5)
+        out.append({"name": name, "text": text, "cls": cls, "lo": 0, "hi": hi, "frames": frames,
+                    "valuations": vals, "h100": h100})
+    return out

@@ -220,3 +220,38 @@ def test_witness_cert_decoding():
     key = (0 << 27) | (0 << 3) | 0
     c = mk.witness_cert(prog, "[]p -> p", "K", 1, 0, None, key)
     assert c.n == 1 and c.succ[0] == 0 and c.val[0] == 0 and mk.certify_struct(c) == 1
+
+
+def test_valuation_split_plan():
+    """Host planning of the valuation split (no GPU calls): a one-formula
+    layer of 32 frame words is far below a full grid, so it splits and needs
+    a 32-word frame bitmap and a tile counter after the lists, but no extra
+    launch; a layer forced unsplit, or whose formulas have too few
+    valuations to share out, needs neither."""
+    cfg_auto = mk.census_cfg(("K",), 4, 4, 0, 0, 0, 1024, None, max_depth=4)
+    cfg_one = mk.census_cfg(("K",), 4, 4, 0, 0, 0, 1024, None, max_depth=4, vsplit=1)
+    lists = mk.census_workspace_size(cfg_one, 1)
+    assert lists > 0
+    assert mk.census_workspace_size(cfg_auto, 1) == -(-lists // 256) * 256 + 256
+    assert mk.census_launches(cfg_auto, 1) == mk.census_launches(cfg_one, 1) == 2
+    # at most one variable: 16 valuations at n = 4, one 128-row block, no split
+    cfg_k1 = mk.census_cfg(("K",), 4, 4, 0, 0, 0, 1024, None, max_depth=4, max_vars=1)
+    assert mk.census_workspace_size(cfg_k1, 1) == lists
+    cfg_k2 = mk.census_cfg(("K",), 4, 4, 0, 0, 0, 1024, None, max_depth=4, max_vars=2)
+    assert mk.census_workspace_size(cfg_k2, 1) > lists
+    # 5 formulas: the bitmap holds 5 x 32 words
+    assert mk.census_workspace_size(cfg_auto, 5) == -(-lists // 256) * 256 + 5 * 32 * 4 + (256 - 5 * 32 * 4 % 256) % 256
+    # a layer that fills the GPU (every five-world K frame, 64 formulas) does not split
+    full5 = mk.census_cfg(("K",), 5, 5, 0, 0, 0, mk.NO_KEY, None, max_depth=4)
+    full5_one = mk.census_cfg(("K",), 5, 5, 0, 0, 0, mk.NO_KEY, None, max_depth=4, vsplit=1)
+    assert mk.census_workspace_size(full5, 64) == mk.census_workspace_size(full5_one, 64)
+    # T window: at n = 4 the diagonal is bits 0, 5, 10, 15 and compact index 255
+    # sets the off-diagonal bits 1-4 and 6-9, so K index 34,815 = 2^15 + 2^10 +
+    # (2^10 - 1); the T frames below 34,816 are compact indices [0, 256), 8 words
+    t_auto = mk.census_cfg(("T",), 4, 4, 0, 0, 0, 34816, None, max_depth=4)
+    t_one = mk.census_cfg(("T",), 4, 4, 0, 0, 0, 34816, None, max_depth=4, vsplit=1)
+    lt = mk.census_workspace_size(t_one, 3)
+    assert mk.census_workspace_size(t_auto, 3) == -(-lt // 256) * 256 + 256   # 3 x 8 words = 96 B
+    # more than 4096 chunks is an argument error
+    bad = mk.census_cfg(("K",), 4, 4, 0, 0, 0, 1024, None, max_depth=4, vsplit=4097)
+    assert mk.census_workspace_size(bad, 1) == 0
