@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", default=None,
-                    help="census5:F -- run the K n=5 layer of the first F five-world formulas twice "
+                    help="matched:R -- row R of --workload matched, twice; "
+                         "census5:F -- run the K n=5 layer of the first F five-world formulas twice "
                          "(a warm-up and the launch an ncu capture selects with -s 1 -c 1), then exit; "
                          "separation:P -- the same for the first P separation pairs at n=6; "
                          "stress:P -- the first P mining candidates on 2^16 12-world relations (two "
@@ -758,6 +759,10 @@ def run_profile_case(spec):
         job = E.CensusJob(W.census5_formulas()[:count], ("K",), 5, 5, samples=S, seed=SEED)
     elif kind == "separation":
         job = E.SeparateJob(W.separation_pairs(4)[:count], 6, 6, frame_lo=0, frame_hi=1 << 30)
+    elif kind == "matched":
+        # row `count` of the matched single-formula workload (0 = Table 1's)
+        r = W.matched_rows()[count]
+        job = E.CensusJob([r["text"]], (r["cls"],), 5, 5, samples=0, frame_lo=r["lo"], frame_hi=r["hi"])
     elif kind == "mlp":
         # the tcgen05 first layer on `count` pairs (full feature width), twice
         from paper_2606_15437_gb300 import mk
