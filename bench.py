@@ -43,6 +43,9 @@ LOP3_PER_SM_CLK = 64        # 3-input logic ops per SM per clock (4 SMSPs x 16 A
 # a K n=5 launch: 92,928 B for the 16-formula ncu capture of this kernel
 # (bench.py --profile-case census5:16), scaled by the formulas processed.
 DRAM_BYTES_PER_FORMULA_K5 = 92928 / 16
+# DRAM bytes (read + write) of one census_layer_kernel<5, 8, 256, 1> launch of
+# Table 1's matched row (bench.py --profile-case matched:0, ncu capture)
+DRAM_BYTES_MATCHED_T1 = 119296
 
 
 def parse():
@@ -887,8 +890,11 @@ def run_matched(args):
                       "l2": "flushed (256 MB write) before every step"},
            "roofline": {"bound": "alu", "kernel": "census_layer_kernel<5> (one formula, valuations split)",
                         "achieved": ops / (row["ms"] / 1e3) / 1e12, "peak": peak,
-                        "unit": "Tops/s (3-input logic ops)", "frac": row["logic_ops_frac"], "traffic": None,
-                        "note": "a 0.27 G-evaluation launch: launch latency bounds it"},
+                        "unit": "Tops/s (3-input logic ops)", "frac": row["logic_ops_frac"],
+                        "traffic": DRAM_BYTES_MATCHED_T1,
+                        "traffic_note": "bytes per launch, from an ncu capture of this row",
+                        "note": "a 0.27 G-evaluation launch of 32-valuation chunks (ALU 62 % in its "
+                                "active cycles under ncu)"},
            "e2e": {"value": row["evals"] / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
                    "h2d_bytes_per_step": h_prog.numel(), "d2h_bytes_per_step": h_out.numel() * 8},
            "gpu_launches": row["launches"] * args.steps, "clocks": clk, "rows": rows}
