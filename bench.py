@@ -40,9 +40,9 @@ SMS = 152
 SM_MAX_MHZ = 2070.0
 LOP3_PER_SM_CLK = 64        # 3-input logic ops per SM per clock (4 SMSPs x 16 ALU lanes)
 # DRAM bytes (read + write) of census_layer_kernel<5, 8, 256> per formula of
-# a K n=5 launch: 92,928 B for the 16-formula ncu capture of this kernel
+# a K n=5 launch: 88,576 B for the 16-formula ncu capture of this kernel
 # (bench.py --profile-case census5:16), scaled by the formulas processed.
-DRAM_BYTES_PER_FORMULA_K5 = 92928 / 16
+DRAM_BYTES_PER_FORMULA_K5 = 88576 / 16
 # DRAM bytes (read + write) of one census_layer_kernel<5, 8, 256, 1> launch of
 # Table 1's matched row (bench.py --profile-case matched:0, ncu capture)
 DRAM_BYTES_MATCHED_T1 = 119296
