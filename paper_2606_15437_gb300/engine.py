@@ -26,7 +26,12 @@ def _dev_bytes(arr, device):
 
 
 class CensusJob:
-    """One census batch: texts x classes x n in [n_min, n_max]."""
+    """One census batch: texts x classes x n in [n_min, n_max].
+
+    frame_lo/frame_hi restrict every layer to frames whose K index lies in
+    [frame_lo, frame_hi).  vsplit steers how a layer too small to fill the
+    GPU shares its valuations over the grid (0 automatic, 1 never, v > 1
+    chunks); it never changes the results."""
 
     def __init__(self, texts=None, classes=CLASSES, n_min=1, n_max=5, samples=256, seed=2,
                  device="cuda", tune=None, frame_lo=0, frame_hi=mk.NO_KEY, progs=None,

@@ -290,6 +290,7 @@ def class_mask(classes):
 
 def census_cfg(classes, n_min, n_max, samples=0, d_samples=0, frame_lo=0, frame_hi=NO_KEY, tune=None,
                max_depth=0, vsplit=0, max_vars=0):
+    """An mk_census_cfg (field meanings in include/mk.h)."""
     cfg = mk_census_cfg()
     cfg.max_depth = max_depth
     cfg.max_vars = max_vars
