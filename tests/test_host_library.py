@@ -255,3 +255,31 @@ def test_valuation_split_plan():
     # more than 4096 chunks is an argument error
     bad = mk.census_cfg(("K",), 4, 4, 0, 0, 0, 1024, None, max_depth=4, vsplit=4097)
     assert mk.census_workspace_size(bad, 1) == 0
+
+
+def test_c_program_uses_the_abi(tmp_path):
+    """The header is plain C: a C99 program (tests/c_abi_check.c) compiles
+    against include/mk.h with -pedantic -Werror, links libmk.so and gets the
+    same answers as the binding (host-only calls)."""
+    import shutil
+    import subprocess
+    from paper_2606_15437_gb300 import build as mkbuild
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lib = mkbuild.build()
+    libdir = os.path.dirname(lib)
+    exe = str(tmp_path / "c_abi_check")
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c_abi_check.c"), "-o", exe, "-L", libdir, "-lmk",
+                    "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    got = {line.split()[0]: line.split()[1:] for line in out.splitlines()}
+    assert got["version"] == ["1"]
+    prog = mk.compile("[]p -> p")
+    assert got["compile"] == ["0", "nvars", str(int(prog.nvars)), "nodes", str(int(prog.nodes))]
+    assert got["syntax"] == ["-1", "ok"]
+    assert got["strerror"] == ["set"]
+    assert got["certify"] == ["1"] and got["certify_dead_end"] == ["0"]
+    assert got["s4_5"] == ["6942"] and got["s5_5"] == ["52"]
+    assert got["workspace"] == ["positive"] and got["workspace_bad"] == ["0"]
