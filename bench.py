@@ -626,6 +626,8 @@ def run_atlas(args):
     E.Atlas(W.census5_formulas()[:256], 3).compute()                      # warm-up
     clocks = ClockSampler(gpu_smi_id(dev, 0))
     corpus = E.Atlas(W.census5_formulas(), 3)
+    corpus.compute()                                                      # allocates its output
+    torch.cuda.synchronize()
     ev = [_events() for _ in range(3)]
     ev[0][0].record()
     corpus.compute()

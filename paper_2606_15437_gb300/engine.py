@@ -769,7 +769,9 @@ class Atlas:
             raise mk.MkError(mk.status_error(st), "device status 0x%x" % st)
 
     def compute(self, stream=None):
-        self.counts = torch.empty((self.B, self.F), dtype=torch.int32, device=self.device)
+        """Enqueue the counts (into the same buffer on every call)."""
+        if getattr(self, "counts", None) is None:
+            self.counts = torch.empty((self.B, self.F), dtype=torch.int32, device=self.device)
         mk.atlas_counts_raw(self.d_progs.data_ptr(), self.B, self.n, self.counts.data_ptr(), self.F,
                             self.d_status.data_ptr(), _stream_ptr(stream))
         return self.counts
