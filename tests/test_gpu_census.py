@@ -195,6 +195,8 @@ SPLIT_CASES = [
     ("[](p0 -> <>p1) -> <>[]p0 | p2", "S4", 4, (0, mk.NO_KEY), 0),
     ("[]p0 & <>p1 -> <>(p2 & p3)", "K", 5, (0, 2048), 256),
     ("<>[](p0 -> <>(p1 & ~p2)) -> [][]p0", "K", 5, (96, 192), 0),
+    # four variables at five worlds, all 2^20 valuations, on a part-filled word
+    ("<>(p0 & p1) -> [](p2 | ~p3)", "K", 5, (3, 7), 0),
 ]
 
 
