@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -143,7 +144,7 @@ class ClockSampler:
 
     def __init__(self, gpu_id):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+        self.path = os.path.join(tempfile.gettempdir(), "mk_clocks_%d.csv" % os.getpid())
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
@@ -353,7 +354,7 @@ def run_mk(args):
         torch.distributed.destroy_process_group()
 
 
-# ------------------------------------------------------- other §8 workloads
+# ---------------------------------------------------------- other workloads
 
 def _events():
     import torch

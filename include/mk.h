@@ -22,7 +22,7 @@
  *     only global state is a mutex-guarded cache of the kernel attributes it
  *     has set on each device (and the fixed scratch of mk_census_noalloc).
  *
- * Encodings (the readings of the paper behind them are listed in the design doc)
+ * Encodings (readings of the paper where it leaves them open)
  *   - World w of an n-world frame is bit w of a mask; full = 2^n - 1 (Sec. 3).
  *   - Frame (K) index f: R(w,v) holds iff bit w*n+v of f is set, so the
  *     successor mask succ[w] is bits [w*n, w*n+n) of f.

@@ -28,7 +28,7 @@
  *                 of Sec. 7 / Table 2 on up to 16 worlds, and the same
  *                 separation order over an explicit list of relations
  *
- * Readings of the paper where it is silent (each is listed in the design doc):
+ * Readings of the paper where it is silent:
  *   - frame index f of an n-world frame: R(w,v) is bit (w*n+v) of f
  *     (so successor mask succ[w] is bits [w*n, w*n+n) of f);
  *   - valuation index x: p_i holds at w iff bit (i*n+w) of x is set;
@@ -495,8 +495,8 @@ int orc_threads(void) { return omp_get_max_threads(); }
  * n <= 16 worlds: the named stress templates (paths, reverse paths, loops,
  * forks, cycles, stars, sparse and dense frames) and the adversarial relation
  * generators of Table 2.  The paper names these families without fixing a
- * construction; the readings below are the ones this project uses (each is
- * listed in the design doc).  A relation is returned as successor masks:
+ * construction; the readings below are the ones this project uses.  A
+ * relation is returned as successor masks:
  * bit v of succ[w] is set iff R(w, v).
  */
 

@@ -4,7 +4,7 @@ This module only makes inputs: formula texts, formula pairs and the tables of
 sampled valuations.  It holds none of the evaluation arithmetic, so both the
 CUDA path and the CPU oracle can take their inputs from it.
 
-Workloads (the recipe is restated in the design doc):
+Workloads:
 
 * ``pr1_formulas``      -- 64 random formulas over p, q (length <= 12, modal
   depth <= 3) plus the K, T and 4 axioms; census over n <= 3, all valuations.
