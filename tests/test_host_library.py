@@ -283,3 +283,35 @@ def test_c_program_uses_the_abi(tmp_path):
     assert got["certify"] == ["1"] and got["certify_dead_end"] == ["0"]
     assert got["s4_5"] == ["6942"] and got["s5_5"] == ["52"]
     assert got["workspace"] == ["positive"] and got["workspace_bad"] == ["0"]
+
+
+def test_uneven_plan_covers_every_layer_once():
+    """mk_plan_uneven (host only): over its work items, every job's layers
+    (its class at n = 1 .. its n_max) are covered exactly once, frame word
+    by frame word, and no item holds jobs of another class or a smaller
+    n_max."""
+    rng = random.Random(17)
+    texts = [W.random_formula(rng, rng.randint(1, 30), rng.randint(0, 5), rng.randint(0, 3)) for _ in range(120)]
+    progs = mk.compile_batch(texts)
+    jobs = np.zeros(len(texts), mk.JOB_DTYPE)
+    jobs["prog"] = np.arange(len(texts))
+    jobs["cls"] = [rng.randrange(4) for _ in texts]
+    jobs["n_max"] = [rng.choice((2, 3, 4, 5)) for _ in texts]
+    for tiles in (None, (4, 8, 16, 32)):
+        plan, info = mk.plan_uneven(progs, jobs, 64, tiles=tiles)
+        jl = plan[info.list_off:info.list_off + 4 * info.nlist].view(np.uint32)
+        item = np.dtype([("lbeg", "<u4"), ("np", "<u2"), ("n", "u1"), ("cls", "u1"), ("w0", "<u8"), ("w1", "<u8")])
+        items = plan[info.items_off:info.items_off + info.nitems * 24].view(item)
+        cover = {}
+        for it in items:
+            for j in jl[int(it["lbeg"]):int(it["lbeg"]) + int(it["np"])]:
+                assert jobs["cls"][j] == it["cls"] and jobs["n_max"][j] >= it["n"]
+                cover.setdefault((int(j), int(it["n"])), []).append((int(it["w0"]), int(it["w1"])))
+        names = ("K", "T", "S4", "S5")
+        for j in range(len(texts)):
+            for n in range(1, int(jobs["n_max"][j]) + 1):
+                words = -(-mk.class_frames(names[jobs["cls"][j]], n) // 32)
+                spans = sorted(cover.pop((j, n)))
+                assert spans[0][0] == 0 and spans[-1][1] == words
+                assert all(a[1] == b[0] for a, b in zip(spans, spans[1:]))
+        assert not cover
