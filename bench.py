@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", default=None,
-                    help="matched:R -- row R of --workload matched, twice; "
+                    help="matched:R -- row R of --workload matched, twice; uneven:F -- the first F "
+                         "formulas of the uneven batch, one persistent launch twice; "
                          "census5:F -- run the K n=5 layer of the first F five-world formulas twice "
                          "(a warm-up and the launch an ncu capture selects with -s 1 -c 1), then exit; "
                          "separation:P -- the same for the first P separation pairs at n=6; "
@@ -776,6 +777,16 @@ def run_profile_case(spec):
         job = E.CensusJob(W.census5_formulas()[:count], ("K",), 5, 5, samples=S, seed=SEED)
     elif kind == "separation":
         job = E.SeparateJob(W.separation_pairs(4)[:count], 6, 6, frame_lo=0, frame_hi=1 << 30)
+    elif kind == "uneven":
+        # the first `count` formulas of the uneven batch, one persistent
+        # queue launch per run (units 4, 128 threads, 8/8/4/4 tiles)
+        uj = E.UnevenJob(W.uneven_formulas(3)[:count], samples=64, seed=3, tiles=(8, 8, 4, 4),
+                         tune={"units": 4, "block": 128})
+        uj.launch()
+        uj.launch()
+        torch.cuda.synchronize()
+        print("profile case %s done" % spec)
+        return
     elif kind == "matched":
         # row `count` of the matched single-formula workload (0 = Table 1's)
         r = W.matched_rows()[count]
