@@ -401,3 +401,36 @@ def test_sampled_pair_scan_matches_explicit_frames():
             first = (s, 0, int(d[0]))
             break
     assert (r["split"][:3] if r["split"] else None) == first
+
+
+# ------------------------------------------------- frontier (Sec. 6, Prop. 3)
+
+def _constant_free(nodes):
+    """Every formula text over p, q with ~, [], <>, &, |, -> of exactly
+    `nodes` nodes (atoms included)."""
+    if nodes == 1:
+        return ["p", "q"]
+    out = []
+    for u in ("~", "[]", "<>"):
+        out += [u + "(" + a + ")" for a in _constant_free(nodes - 1)]
+    for i in range(1, nodes - 1):
+        for a in _constant_free(i):
+            for b in _constant_free(nodes - 1 - i):
+                out += ["(" + a + " " + op + " " + b + ")" for op in ("&", "|", "->")]
+    return out
+
+
+def test_frontier_refutable_formulas_need_at_most_two_worlds():
+    # Prop. 3 and Sec. 6: no K-refutable constant-free formula over two
+    # variables in the bounded corpus needs three worlds.  Checked for every
+    # such formula of at most six nodes (7,040 of them), through three worlds.
+    forms = [f for n in range(1, 7) for f in _constant_free(n)]
+    assert len(forms) == 2 + 6 + 30 + 162 + 954 + 5886
+    least = {}
+    for f in forms:
+        for n in (1, 2, 3):
+            if oracle.census(f, "K", n)["cm_count"]:
+                least[n] = least.get(n, 0) + 1
+                break
+    assert 3 not in least
+    assert least[1] > 0 and least[2] > 0
