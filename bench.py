@@ -47,6 +47,13 @@ DRAM_BYTES_PER_FORMULA_K5 = 88576 / 16
 # DRAM bytes (read + write) of one census_layer_kernel<5, 8, 256, 1> launch of
 # Table 1's matched row (bench.py --profile-case matched:0, ncu capture)
 DRAM_BYTES_MATCHED_T1 = 119296
+# ncu captures of smaller cases, per unit they process (scaled in the bench):
+# mlp_l1_tc_ws_kernel on 77,824 pairs: 10.06 MB read + 24.81 MB written
+DRAM_BYTES_PER_PAIR_MLP = (10058240 + 24808704) / 77824
+# stress_kernel<12, 2, 1, 8, 256> on 2^16 relations: 1.34 MB read, 0 written
+DRAM_BYTES_PER_RELATION_STRESS = 1339392 / 65536
+# census_queue_kernel<5, 4, 128> on 2,000 uneven-batch formulas: 1.41 MB read
+DRAM_BYTES_PER_FORMULA_UNEVEN = 1411840 / 2000
 
 
 def parse():
@@ -446,7 +453,10 @@ def run_uneven(args):
            "speedup_vs_per_bucket": ms_b / ms,
            "roofline": {"bound": "alu", "kernel": "census_queue_kernel", "achieved": ops / (ms / 1e3) / 1e12,
                         "peak": peak, "unit": "Tops/s (3-input logic ops)", "frac": ops / (ms / 1e3) / 1e12 / peak,
-                        "traffic": None, "note": "step time (graph replay) in the denominator"},
+                        "traffic": DRAM_BYTES_PER_FORMULA_UNEVEN * len(items),
+                        "traffic_note": "bytes per launch, scaled by formulas from a 2,000-formula ncu capture "
+                                        "(bench.py --profile-case uneven:2000)",
+                        "note": "step time (graph replay) in the denominator"},
            "e2e": {"value": evals / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
                    "h2d_bytes_per_step": sum(h.numel() * h.element_size() for h in h_in),
                    "d2h_bytes_per_step": h_out.numel() * 8},
@@ -555,6 +565,10 @@ def run_adversarial(args):
                       "late_template_witness": late_tpl, "mining_seconds": t_mine},
            "roofline": {"bound": "alu", "kernel": "stress_kernel", "achieved": achieved, "peak": peak,
                         "unit": "Tops/s (3-input logic ops)", "frac": achieved / peak,
+                        "traffic": DRAM_BYTES_PER_RELATION_STRESS * args.relations,
+                        "traffic_note": "bytes per 12-world launch (the relation words, read once), scaled by "
+                                        "relations from a 2^16-relation ncu capture (bench.py --profile-case "
+                                        "stress:64)",
                         "peak_basis": "%d SMs x %d logic ops/clk x %.0f MHz" % (SMS, LOP3_PER_SM_CLK, SM_MAX_MHZ)},
            "gpu_seconds": gpu_s, "evals": evals, "by_generator": by_gen,
            "top_mining": [{k: r[k] for k in ("phi", "psi", "a", "template", "J")} for r in mine[:6]],
@@ -757,7 +771,11 @@ def run_mlp(args):
            "higher_is_better": True, "vs_baseline": None, "dtype": "bf16", "data": "synthetic (seeded)",
            "config": {"workload": "MLP layer 1: 155,648 pairs x 8,192 features x 256 hidden", "l2": "flushed"},
            "roofline": {"bound": "tensor", "kernel": "mlp_l1_tc_ws_kernel", "achieved": tc, "peak": peak,
-                        "unit": "TFLOP/s", "frac": tc / peak, "peak_basis": "measured cuBLAS bf16 (burst)"},
+                        "unit": "TFLOP/s", "frac": tc / peak, "peak_basis": "measured cuBLAS bf16 (burst)",
+                        "traffic": DRAM_BYTES_PER_PAIR_MLP * B,
+                        "traffic_note": "bytes per launch, scaled by pairs from a 77,824-pair ncu capture "
+                                        "(bench.py --profile-case mlp:77824); part of that capture's output "
+                                        "was still in L2, so writes are a lower bound"},
            "ms": res, "tcgen05_single_group_tflops": flops / (res["tc"] / 1e3) / 1e12,
            "mma_sync_tflops": flops / (res["mma"] / 1e3) / 1e12,
            "speedup_vs_mma_sync": res["mma"] / res["ws"], "clocks": clk}
