@@ -434,3 +434,16 @@ def test_frontier_refutable_formulas_need_at_most_two_worlds():
                 break
     assert 3 not in least
     assert least[1] > 0 and least[2] > 0
+
+
+def test_matched_rows_have_the_table_shapes():
+    # Table 4's frames x valuations per row: the valuation count is all
+    # valuations of the row's variables on five worlds, and the T row's
+    # window holds exactly its 2,049 reflexive frames (counted by the oracle)
+    for r in W.matched_rows():
+        assert 2 ** (5 * oracle.nvars(r["text"])) == r["valuations"], r["name"]
+        if r["cls"] == "K":
+            assert (r["lo"], r["hi"]) == (0, r["frames"])
+    t = [r for r in W.matched_rows() if r["cls"] == "T"][0]
+    got = oracle.census(t["text"], "T", 5, f_lo=t["lo"], f_hi=t["hi"])
+    assert got["frames"] == t["frames"] == 2049
