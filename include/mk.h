@@ -204,9 +204,15 @@ int mk_census(const mk_program *d_progs, int32_t nprog, const mk_census_cfg *cfg
    exits.  Configurations whose S4/S5 frame lists exceed that limit (S4 or
    S5 at n = 6) are rejected with MK_E_WORKSPACE before anything is
    launched; layers split their valuations only when the split bitmap also
-   fits (mk_census_workspace_size <= the limit).  The first call on a device looks up the array's address
-   (cudaGetSymbolAddress) with that device current; make that first call
-   before any stream capture.  All calls share the one array, and it keeps
+   fits (mk_census_workspace_size <= the limit).  Every call made outside
+   stream capture looks up the array's address on the current device
+   (cudaGetSymbolAddress, which allocates nothing) and remembers it; a call
+   made while its stream is being captured uses the address remembered for
+   that device, or looks it up if there is none.  So a device reset
+   (cudaDeviceReset, or the primary context torn down and re-created)
+   between calls is harmless, but after one make an uncaptured call before
+   capturing, and make the first call on a device before any stream
+   capture.  All calls share the one array, and it keeps
    the last call's contents: every part of it that a call reads is written
    by that call first, but calls whose work overlaps on the GPU (different
    streams, or different host threads) race on it, so serialise them.
@@ -328,8 +334,15 @@ typedef struct {
        sampled << 63 | (n - 1) << 60 | f << 24 | x << 3 | w
    (f: K index or sample number < 2^36; x < 2^21; w < 8), UINT64_MAX if the
    pair agrees everywhere searched.  Relations of sampled sizes come from
-   mk_sample_relation(seed, n, s). */
+   mk_sample_relation(seed, n, s).  The workspace (mk_separate_workspace_size
+   bytes, 16-byte aligned, contents need not be initialised; MK_E_WORKSPACE
+   if smaller) holds the list of pairs still unsplit, rebuilt on the device
+   before every launch so that only those pairs are staged. */
 size_t mk_separate_workspace_size(const mk_separate_cfg *cfg, int32_t npairs);
+/* Kernel launches one mk_separate call with this configuration issues (the
+   keys' initialisation, then an active-pair list and a search per chunk);
+   -1 for an invalid configuration. */
+int64_t mk_separate_launches(const mk_separate_cfg *cfg, int32_t npairs);
 int mk_separate(const mk_program *d_phi, const mk_program *d_psi, int32_t npairs,
                 const mk_separate_cfg *cfg, uint64_t *d_split, int32_t *d_status,
                 void *d_workspace, size_t ws_bytes, void *stream);
@@ -448,6 +461,21 @@ int mk_mlp_w1_tiles(const float *d_params, int32_t features, int32_t hidden, voi
 int mk_mlp_layer1_tc_ws(const uint32_t *d_vec, int32_t features, const int32_t *d_pa, const int32_t *d_pb,
                         int32_t batch, const void *d_w1_tiles, const float *d_b1, float *d_h1, int32_t *d_status,
                         void *stream);
+
+/* The same layer with the iteration limit of its pipeline waits given by the
+   caller (wait_spins >= 1 tests of an mbarrier, each followed by a ~32 ns
+   sleep; mk_mlp_layer1_tc_ws uses 2^24, about two seconds).  A limit that
+   runs out is the failure the bounded waits guard against (a copy or an MMA
+   that never completes): the CTA's roles agree to abort, the bulk copies
+   already issued are waited for on their own barriers, one more
+   tcgen05.commit tracks every MMA already issued and is waited for, the
+   tensor memory is freed, MK_ST_TIMEOUT is OR-ed into *d_status and h1 is
+   left undefined.  The context stays usable.  A small limit makes the waits
+   run out on purpose, which is how the timeout path is tested.
+   MK_E_ARG for wait_spins == 0, otherwise as mk_mlp_layer1_tc_ws. */
+int mk_mlp_layer1_tc_ws_bounded(const uint32_t *d_vec, int32_t features, const int32_t *d_pa, const int32_t *d_pb,
+                                int32_t batch, const void *d_w1_tiles, const float *d_b1, float *d_h1,
+                                int32_t *d_status, uint32_t wait_spins, void *stream);
 
 /* ------------------------------------------- large frames (Sec. 7) */
 /* Separation beyond the exhaustive sizes runs over explicit relations on up

@@ -22,7 +22,9 @@
 //
 // Every wait on an mbarrier is bounded: a thread that gives up sets
 // MK_ST_TIMEOUT, the CTA agrees on it (__syncthreads_or), skips the rest,
-// lets its copies drain and frees its tensor memory before returning.
+// lets its copies drain, waits (bounded) for the MMAs it already issued --
+// one more tcgen05.commit covers all of them -- and only then frees its
+// tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -71,8 +73,8 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait for the completion of the given phase; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (uint32_t i = 0; i < TC_WAIT_SPINS; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t spins = TC_WAIT_SPINS) {
+    for (uint32_t i = 0; i < spins; ++i) {
         if (mbar_test(bar, parity)) return true;
         __nanosleep(64);
     }
@@ -210,6 +212,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_l1_tc_kernel(TcArgs a) {
     }
 
     bool timed_out = false;
+    int mma_blocks = 0;                                          // thread 0: blocks of MMAs issued
     for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % TC_STAGES;
         // the stage refilled now was last read by the MMAs of block kb+AHEAD-STAGES
@@ -252,6 +255,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_l1_tc_kernel(TcArgs a) {
             for (int k = 0; k < TC_KB / 16; ++k)                // K = 16 per MMA: 32 bytes along the row
                 tc_mma(tmem, sw128_desc(ad + k * 32), sw128_desc(bd + k * 32), (kb > 0 || k > 0) ? 1u : 0u);
             tc_commit(smem_addr(&bars[s]));
+            ++mma_blocks;
         }
     }
     cp_async_wait<0>();
@@ -259,6 +263,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_l1_tc_kernel(TcArgs a) {
         if (tid == 0) tc_commit(smem_addr(&bars[TC_STAGES]));
         const bool ok = mbar_wait(smem_addr(&bars[TC_STAGES]), 0);
         timed_out = __syncthreads_or(ok ? 0 : 1) != 0;
+    } else if (tid == 0 && mma_blocks > 0) {
+        // MMAs issued before the abort still read shared memory and write
+        // tensor memory: a last commit tracks all of them; wait for it
+        tc_commit(smem_addr(&bars[TC_STAGES]));
+        mbar_wait(smem_addr(&bars[TC_STAGES]), 0);
     }
     if (timed_out) {
         if (tid == 0) atomicOr(a.status, (int)MK_ST_TIMEOUT);
@@ -329,9 +338,11 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  : "memory");
 }
 
-// Bounded wait that also gives up when another role has aborted.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int *abort) {
-    for (uint32_t i = 0; i < TC_WAIT_SPINS; ++i) {
+// Bounded wait (at most `spins` tests) that also gives up when another
+// role has aborted.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int *abort,
+                                                   uint32_t spins) {
+    for (uint32_t i = 0; i < spins; ++i) {
         if (mbar_test(bar, parity)) return true;
         if (*abort) return false;
         __nanosleep(32);
@@ -368,6 +379,7 @@ struct TcWsArgs {
     const float *b1;
     float *h1;
     int32_t *status;
+    uint32_t spins;            // limit of the role waits (the drains after an abort use TC_WAIT_SPINS)
 };
 
 __global__ void __launch_bounds__(WS_THREADS, 1) mlp_l1_tc_ws_kernel(TcWsArgs a) {
@@ -414,7 +426,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mlp_l1_tc_ws_kernel(TcWsArgs a)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *s_tmem;
     bool ok = true;
-    int bulk_issued = 0;
+    int bulk_issued = 0;       // W1 loader: bulk copies issued
+    int mma_blocks = 0;        // MMA issuer: blocks of MMAs issued
+    bool done_committed = false;
+    const uint32_t spins = a.spins;
 
     if (warp < 4) {
         // ---------------------------------------------------------- producers
@@ -444,7 +459,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mlp_l1_tc_ws_kernel(TcWsArgs a)
             uint2 fa[WS_MT], fb[WS_MT];
             if (kb + 2 < nkb) fetch(kb + 2, fa, fb);
             if (kb >= WS_ASTAGES)
-                ok = mbar_wait_or_abort(emptyA(s), (uint32_t)(((kb - WS_ASTAGES) / WS_ASTAGES) & 1), s_abort);
+                ok = mbar_wait_or_abort(emptyA(s), (uint32_t)(((kb - WS_ASTAGES) / WS_ASTAGES) & 1), s_abort, spins);
             if (!ok) break;
             const bool xr = kb * TC_KB < half;
 #pragma unroll
@@ -474,7 +489,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mlp_l1_tc_ws_kernel(TcWsArgs a)
             }
         }
         if (!ok) *s_abort = 1;
-        if (ok) ok = mbar_wait_or_abort(done, 0, s_abort);
+        if (ok) ok = mbar_wait_or_abort(done, 0, s_abort, spins);
         if (!ok) *s_abort = 1;
     } else if (tid == WS_PRODUCERS + 32) {
         // ---------------------------- W1 loader (its own warp: its polling
@@ -482,7 +497,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mlp_l1_tc_ws_kernel(TcWsArgs a)
         for (int kb = 0; kb < nkb && ok; ++kb) {
             const int s = kb % WS_BSTAGES;
             if (kb >= WS_BSTAGES)
-                ok = mbar_wait_or_abort(emptyB(s), (uint32_t)(((kb - WS_BSTAGES) / WS_BSTAGES) & 1), s_abort);
+                ok = mbar_wait_or_abort(emptyB(s), (uint32_t)(((kb - WS_BSTAGES) / WS_BSTAGES) & 1), s_abort, spins);
             if (!ok) break;
             mbar_expect_tx(fullB(s), TC_B_BYTES);
             mbar_arrive(fullB(s));
@@ -495,8 +510,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mlp_l1_tc_ws_kernel(TcWsArgs a)
         // --------------------------------------------------------- MMA issuer
         for (int kb = 0; kb < nkb && ok; ++kb) {
             const int sa = kb % WS_ASTAGES, sb = kb % WS_BSTAGES;
-            ok = mbar_wait_or_abort(fullB(sb), (uint32_t)((kb / WS_BSTAGES) & 1), s_abort) &&
-                 mbar_wait_or_abort(fullA(sa), (uint32_t)((kb / WS_ASTAGES) & 1), s_abort);
+            ok = mbar_wait_or_abort(fullB(sb), (uint32_t)((kb / WS_BSTAGES) & 1), s_abort, spins) &&
+                 mbar_wait_or_abort(fullA(sa), (uint32_t)((kb / WS_ASTAGES) & 1), s_abort, spins);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t aa = sbase + (uint32_t)sa * WS_A_BYTES, bb = sbase + WS_B_OFF + (uint32_t)sb * TC_B_BYTES;
@@ -508,19 +523,33 @@ __global__ void __launch_bounds__(WS_THREADS, 1) mlp_l1_tc_ws_kernel(TcWsArgs a)
                            sw128_desc(bb + k * 32), (kb > 0 || k > 0) ? 1u : 0u);
             tc_commit(emptyA(sa));
             tc_commit(emptyB(sb));
+            ++mma_blocks;
         }
-        if (ok) tc_commit(done);
-        else *s_abort = 1;
+        if (ok) {
+            tc_commit(done);
+            done_committed = true;
+        } else {
+            *s_abort = 1;
+        }
     }
     __syncthreads();
     const bool aborted = *s_abort != 0;
     if (aborted) {
-        // let bulk copies still in flight land before the CTA's memory goes
-        // (a 32 KB copy takes microseconds; this waits about 100 us)
+        // Nothing asynchronous may outlive the CTA's shared and tensor memory.
         if (tid == WS_PRODUCERS + 32) {
             atomicOr(a.status, (int)MK_ST_TIMEOUT);
-            if (bulk_issued)
-                for (int i = 0; i < 1000; ++i) __nanosleep(100);
+            // the last copy issued into each ring slot completes that slot's
+            // "full" phase (the earlier ones were consumed before the slot was
+            // refilled): wait for those phases
+            const int first = bulk_issued > WS_BSTAGES ? bulk_issued - WS_BSTAGES : 0;
+            for (int kb = first; kb < bulk_issued; ++kb)
+                mbar_wait(fullB(kb % WS_BSTAGES), (uint32_t)((kb / WS_BSTAGES) & 1));
+        } else if (tid == WS_PRODUCERS && mma_blocks > 0) {
+            // one commit after the last MMA tracks every MMA this thread
+            // issued; "done" is committed at most once, so its phase 0 ends
+            // when they all have completed
+            if (!done_committed) tc_commit(done);
+            mbar_wait(done, 0);
         }
     } else if (warp < 4) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -569,9 +598,11 @@ extern "C" int mk_mlp_w1_tiles(const float *d_params, int32_t features, int32_t 
     return cudaGetLastError() == cudaSuccess ? MK_OK : MK_E_CUDA;
 }
 
-extern "C" int mk_mlp_layer1_tc_ws(const uint32_t *d_vec, int32_t features, const int32_t *d_pa, const int32_t *d_pb,
-                                   int32_t batch, const void *d_w1_tiles, const float *d_b1, float *d_h1,
-                                   int32_t *d_status, void *stream) {
+namespace {
+
+int layer1_tc_ws(const uint32_t *d_vec, int32_t features, const int32_t *d_pa, const int32_t *d_pb, int32_t batch,
+                 const void *d_w1_tiles, const float *d_b1, float *d_h1, int32_t *d_status, uint32_t spins,
+                 void *stream) {
     using namespace mkd;
     if (features <= 0 || features % 128 || batch < 0 || !d_status) return MK_E_ARG;
     if (batch == 0) return MK_OK;
@@ -588,8 +619,26 @@ extern "C" int mk_mlp_layer1_tc_ws(const uint32_t *d_vec, int32_t features, cons
     a.b1 = d_b1;
     a.h1 = d_h1;
     a.status = d_status;
+    a.spins = spins;
     mlp_l1_tc_ws_kernel<<<(batch + WS_PAIRS - 1) / WS_PAIRS, WS_THREADS, WS_SMEM_BYTES, (cudaStream_t)stream>>>(a);
     return cudaGetLastError() == cudaSuccess ? MK_OK : MK_E_CUDA;
+}
+
+}  // namespace
+
+extern "C" int mk_mlp_layer1_tc_ws(const uint32_t *d_vec, int32_t features, const int32_t *d_pa, const int32_t *d_pb,
+                                   int32_t batch, const void *d_w1_tiles, const float *d_b1, float *d_h1,
+                                   int32_t *d_status, void *stream) {
+    return layer1_tc_ws(d_vec, features, d_pa, d_pb, batch, d_w1_tiles, d_b1, d_h1, d_status, mkd::TC_WAIT_SPINS,
+                        stream);
+}
+
+extern "C" int mk_mlp_layer1_tc_ws_bounded(const uint32_t *d_vec, int32_t features, const int32_t *d_pa,
+                                           const int32_t *d_pb, int32_t batch, const void *d_w1_tiles,
+                                           const float *d_b1, float *d_h1, int32_t *d_status, uint32_t wait_spins,
+                                           void *stream) {
+    if (wait_spins == 0) return MK_E_ARG;
+    return layer1_tc_ws(d_vec, features, d_pa, d_pb, batch, d_w1_tiles, d_b1, d_h1, d_status, wait_spins, stream);
 }
 
 

@@ -110,6 +110,7 @@ _SIGS = {
                                        ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
                                        ctypes.POINTER(mk_cert)]),
     "mk_separate_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(mk_separate_cfg), ctypes.c_int32]),
+    "mk_separate_launches": (ctypes.c_int64, [ctypes.POINTER(mk_separate_cfg), ctypes.c_int32]),
     "mk_separate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                    ctypes.POINTER(mk_separate_cfg), ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
@@ -209,6 +210,10 @@ _SIGS = {
     "mk_mlp_layer1_tc_ws": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p]),
+    "mk_mlp_layer1_tc_ws_bounded": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                                   ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                                                   ctypes.c_void_p]),
     "mk_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mk_status_error": (ctypes.c_int, [ctypes.c_int32]),
     "mk_version": (ctypes.c_int, []),
@@ -450,6 +455,11 @@ def separate_workspace_size(cfg, npairs):
     return int(lib().mk_separate_workspace_size(ctypes.byref(cfg), npairs))
 
 
+def separate_launches(cfg, npairs):
+    """Kernel launches of one mk_separate call (its own count)."""
+    return int(lib().mk_separate_launches(ctypes.byref(cfg), npairs))
+
+
 # ------------------------------------------------------ uneven batches
 
 def plan_uneven(progs, jobs, samples, tiles=None, tune=None):
@@ -561,6 +571,12 @@ def mlp_w1_tiles_raw(d_params, features, hidden, d_tiles, stream):
 def mlp_layer1_tc_ws_raw(d_vec, features, d_pa, d_pb, batch, d_tiles, d_b1, d_h1, d_status, stream):
     _check(lib().mk_mlp_layer1_tc_ws(d_vec, features, d_pa, d_pb, batch, d_tiles, d_b1, d_h1, d_status, stream),
            "mk_mlp_layer1_tc_ws")
+
+
+def mlp_layer1_tc_ws_bounded_raw(d_vec, features, d_pa, d_pb, batch, d_tiles, d_b1, d_h1, d_status, wait_spins,
+                                 stream):
+    _check(lib().mk_mlp_layer1_tc_ws_bounded(d_vec, features, d_pa, d_pb, batch, d_tiles, d_b1, d_h1, d_status,
+                                             wait_spins, stream), "mk_mlp_layer1_tc_ws_bounded")
 
 
 def mlp_layer1_mma_raw(d_vec, features, d_pa, d_pb, batch, d_w1t, d_b1, d_h1, stream):

@@ -128,3 +128,43 @@ def test_infer_tc_matches_rounded_reference():
 def test_layer1_tc_rejects_bad_shapes():
     with pytest.raises(mk.MkError):
         mk.mlp_layer1_tc_raw(8, 192, 8, 8, 4, 16, 8, 16, 8, 0)       # features % 128
+
+
+def test_timeout_path_aborts_cleanly_and_next_call_is_exact():
+    """Every pipeline wait of the warp-specialised layer is bounded.  With a
+    limit of one test per wait the waits run out (a bulk copy or an MMA takes
+    longer than one test): the call must report MK_ST_TIMEOUT through the
+    status word (MK_E_TIMEOUT), drain its copies and MMAs, free its tensor
+    memory and leave the context usable, so that the next normal call on the
+    same stream gives the float64-checked result."""
+    F, B = 8192, 700
+    vec, pa, pb = _problem(F, B, 31)
+    net = E().MLP(F, H, seed=32)
+    dv = torch.from_numpy(vec.view(np.int32).copy()).cuda()
+    tpa, tpb = torch.from_numpy(pa).cuda(), torch.from_numpy(pb).cuda()
+    tiles = torch.empty(mk.mlp_w1_tiles_bytes(F), dtype=torch.uint8, device="cuda")
+    mk.mlp_w1_tiles_raw(net.params.data_ptr(), F, H, tiles.data_ptr(), 0)
+    b1 = net.params[F * H:F * H + H]
+    h1 = torch.zeros((B, H), dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    args = (dv.data_ptr(), F, tpa.data_ptr(), tpb.data_ptr(), B, tiles.data_ptr(), b1.data_ptr(), h1.data_ptr(),
+            st.data_ptr())
+    for _ in range(2):
+        st.zero_()
+        mk.mlp_layer1_tc_ws_bounded_raw(*args, 1, 0)
+        torch.cuda.synchronize()
+        assert mk.status_error(int(st.item())) == -11          # MK_E_TIMEOUT
+    with pytest.raises(mk.MkError):
+        mk.mlp_layer1_tc_ws_bounded_raw(*args, 0, 0)            # a zero limit is rejected
+    st.zero_()
+    h1.fill_(-7.0)
+    mk.mlp_layer1_tc_ws_raw(*args, 0)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    X = _features(vec, pa, pb)
+    w1t = torch.empty((H, F), dtype=torch.bfloat16, device="cuda")
+    mk.mlp_w1t_bf16_raw(net.params.data_ptr(), F, H, w1t.data_ptr(), 0)
+    W1 = w1t.float().cpu().numpy().astype(np.float64).T
+    want = np.maximum(X @ W1 + b1.cpu().numpy().astype(np.float64), 0.0)
+    scale = max(1.0, float(np.abs(want).max()))
+    assert np.abs(h1.cpu().numpy() - want).max() <= 2e-5 * scale * np.sqrt(F / 128)
