@@ -12,9 +12,12 @@
 //
 // The array is a file-scope __device__ variable, so every GPU that loads
 // the library holds MK_NOALLOC_SCRATCH_BYTES of it until the process exits.
-// Host code cannot use the variable's name as a device address; the first
-// call on each device (with that device current) asks the runtime for the
-// address with cudaGetSymbolAddress and caches it.  Nothing here calls
+// Host code cannot use the variable's name as a device address; a call
+// asks the runtime for the address on the current device with
+// cudaGetSymbolAddress (a lookup: it allocates nothing).  Calls outside
+// stream capture look it up every time, so an address made stale by a
+// device reset is never used; calls on a capturing stream use the address
+// the last uncaptured call on that device found.  Nothing here calls
 // cudaMalloc, cudaFree or any allocating routine.
 #include <cuda_runtime.h>
 
@@ -31,14 +34,19 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void *g_scratch_ptr[kMaxDevices];
 
-// Device address of g_census_scratch on the current device (set up once
-// per device).
-int scratch_address(void **out) {
+// Device address of g_census_scratch on the current device: looked up
+// afresh unless `stream` is being captured (then the address remembered for
+// the device, looked up only if there is none).
+int scratch_address(cudaStream_t stream, void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return MK_E_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return MK_E_ARG;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    bool capturing = true;
+    if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess) capturing = cs != cudaStreamCaptureStatusNone;
+    else (void)cudaGetLastError();   // e.g. the legacy stream queried during another thread's capture
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_ptr[dev]) {
+    if (!capturing || !g_scratch_ptr[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_census_scratch) != cudaSuccess || !p) return MK_E_CUDA;
         g_scratch_ptr[dev] = p;
@@ -59,7 +67,7 @@ extern "C" int mk_census_noalloc(const mk_program *d_progs, int32_t nprog, const
     if (need == 0) return MK_E_ARG;
     if (need > MK_NOALLOC_SCRATCH_BYTES) return MK_E_WORKSPACE;
     void *scratch = nullptr;
-    const int rc = scratch_address(&scratch);
+    const int rc = scratch_address((cudaStream_t)stream, &scratch);
     if (rc != MK_OK) return rc;
     return mk_census(d_progs, nprog, cfg, d_out, d_status, scratch, MK_NOALLOC_SCRATCH_BYTES, stream);
 }
