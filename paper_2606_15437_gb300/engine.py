@@ -119,6 +119,34 @@ def lop3_per_eval(prog, n):
     return (n * int(prog["n_bool"]) + n * n * int(prog["n_modal"]) + n) / 32.0
 
 
+_SOURCE_OPS = None
+
+
+def source_op_counts(text):
+    """(Boolean connectives, modal operators) of the formula as written: the
+    counts of ~, &, |, ->, <-> and of [], <> in its text (before the normal
+    form and constant folding the compiler applies)."""
+    global _SOURCE_OPS
+    if _SOURCE_OPS is None:
+        import re
+        _SOURCE_OPS = re.compile(r"<->|->|\[\]|<>|~|!|&|\||\b(?:not|and|or|box|dia)\b")
+    nb = nm = 0
+    for t in _SOURCE_OPS.findall(text):
+        if t in ("[]", "<>", "box", "dia"):
+            nm += 1
+        else:
+            nb += 1
+    return nb, nm
+
+
+def source_ops_per_eval(text, n):
+    """Algorithmic logic ops per evaluation counted on the source formula:
+    (n * #Boolean + n^2 * #modal + n) / 32 (the bit-sliced minimum of the
+    recurrence of Lemma 1 for 32 frames, with the refutation test)."""
+    nb, nm = source_op_counts(text)
+    return (n * nb + n * n * nm + n) / 32.0
+
+
 class SeparateJob:
     """Distinguishing-pair search for a list of (phi, psi) texts."""
 
@@ -558,11 +586,16 @@ def budget_walk(texts, pa, pb, order, budget, frames_per_n=1 << 20, chunk=4096, 
 
 def proposal_experiment(n_formulas=10000, universe=5_467_766, k=1024, train_identical=100_000,
                         train_other=100_000, budget=5e13, frames_per_n=1 << 20, epochs=8, seed=5,
-                        train_seed=55, methods=("mlp", "random", "pca10"), log=None, device="cuda"):
-    """The learned proposal against random and PCA-10 rankings at an equal
-    exact-evaluation budget (Sec. 9's retrieval protocol with a learned
-    ranker).  Every number comes from libmk kernels; torch only holds
-    buffers (and computes the PCA-10 comparator's projection)."""
+                        train_seed=55, methods=("mlp", "random", "random_identical", "pca10"), log=None,
+                        device="cuda"):
+    """The learned proposal against random, filtered-random and PCA-10
+    rankings at an equal exact-evaluation budget (Sec. 9's retrieval
+    protocol with a learned ranker).  "random_identical" takes the pairs with
+    identical truth vectors first, in random order (only they can agree on
+    every model of at most five worlds), then the rest: the best a ranker
+    can do from the truth vectors without a network.  Every number comes
+    from libmk kernels; torch only holds buffers (and computes the PCA-10
+    comparator's projection)."""
     import time
     t0 = time.time()
     say = log or (lambda *a: None)
@@ -615,6 +648,11 @@ def proposal_experiment(n_formulas=10000, universe=5_467_766, k=1024, train_iden
         orders["mlp"] = torch.argsort(s, descending=True, stable=True).cpu().numpy()
     if "random" in methods:
         orders["random"] = np.random.default_rng(seed + 1).permutation(len(pa))
+    if "random_identical" in methods:
+        same_u = identical_pairs(bits_np, pa, pb)
+        r = np.random.default_rng(seed + 2)
+        orders["random_identical"] = np.concatenate([r.permutation(np.where(same_u)[0]),
+                                                     r.permutation(np.where(~same_u)[0])])
     if "pca10" in methods:
         xf = torch.from_numpy(np.unpackbits(bits_np.view(np.uint8), axis=1, bitorder="little").astype(np.float32)).to(dev)
         xf = xf - xf.mean(0, keepdim=True)
