@@ -1148,3 +1148,164 @@ def allreduce_results(res, group=None):
     k = k64.numpy()
     out[..., 2] = np.where(k == 2 ** 63 - 1, np.uint64(mk.NO_KEY), k.astype(np.uint64))
     return out
+
+
+# ------------------------------------------------------ checkpoint / resume
+#
+# A long census is cut into independent units -- a tile of formulas, one
+# (class, n) layer, one K-index chunk of that layer -- whose results merge
+# exactly: counts add over disjoint frame sets and the witness is the least
+# key (the census's own reduction, Sec. 4).  Every finished unit is appended
+# to a per-rank journal (one line per unit, flushed and fsync'd before the
+# next unit starts, with a CRC so a line torn by a kill is ignored), so a
+# run that is killed between units resumes by skipping every unit found in
+# any rank's journal.
+
+def census_units(nformulas, classes, n_min, n_max, tile=256, frame_chunk=1 << 22):
+    """The units of a census, in a fixed order: (p0, p1, class, n, f_lo,
+    f_hi) for formula tiles [p0, p1), layers (class, n) and K-index chunks
+    [f_lo, f_hi) of the layer (a chunk of the K index holds the chunk's
+    frames of every class)."""
+    out = []
+    for p0 in range(0, nformulas, tile):
+        p1 = min(nformulas, p0 + tile)
+        for c in classes:
+            for n in range(n_min, n_max + 1):
+                kf = 1 << (n * n)
+                for lo in range(0, kf, frame_chunk):
+                    out.append((p0, p1, c, n, lo, min(kf, lo + frame_chunk)))
+    return out
+
+
+def _journal_config(texts, classes, n_min, n_max, samples, seed, tile, frame_chunk):
+    import hashlib
+    h = hashlib.sha256()
+    h.update("\n".join(texts).encode())
+    h.update(repr((tuple(classes), n_min, n_max, samples, seed, tile, frame_chunk)).encode())
+    return h.hexdigest()
+
+
+class CensusJournal:
+    """The append-only journal of one rank's finished units, in
+    ``directory``/census_rank<r>.jsonl; ``finished()`` reads every rank's."""
+
+    def __init__(self, directory, rank, config):
+        import os
+        self.directory = directory
+        self.config = config
+        os.makedirs(directory, exist_ok=True)
+        self.path = os.path.join(directory, "census_rank%d.jsonl" % rank)
+
+    @staticmethod
+    def _line(obj):
+        import json
+        import zlib
+        body = json.dumps(obj, separators=(",", ":"), sort_keys=True)
+        return "%08x %s\n" % (zlib.crc32(body.encode()), body)
+
+    @staticmethod
+    def _parse(line):
+        import json
+        import zlib
+        if not line.endswith("\n") or len(line) < 10:
+            return None                          # torn: the process died while writing it
+        crc, body = line[:8], line[9:-1]
+        try:
+            if int(crc, 16) != zlib.crc32(body.encode()):
+                return None
+            return json.loads(body)
+        except ValueError:
+            return None
+
+    def finished(self):
+        """{unit: [[cm_count, frames_refuted, key] per formula]} from every
+        rank's journal; a journal written for another configuration raises."""
+        import glob
+        out = {}
+        for path in sorted(glob.glob(self.directory + "/census_rank*.jsonl")):
+            with open(path) as f:
+                for line in f:
+                    rec = self._parse(line)
+                    if rec is None:
+                        continue
+                    if rec.get("config") is not None:
+                        if rec["config"] != self.config:
+                            raise ValueError("%s was written for another census configuration" % path)
+                        continue
+                    out[tuple(rec["unit"])] = rec["res"]
+        return out
+
+    def record(self, unit, res):
+        import os
+        new = not os.path.exists(self.path) or os.path.getsize(self.path) == 0
+        torn = False
+        if not new:
+            with open(self.path, "rb") as f:
+                f.seek(-1, os.SEEK_END)
+                torn = f.read(1) != b"\n"
+        with open(self.path, "a") as f:
+            if torn:
+                f.write("\n")                      # end a line torn by a kill; it fails its CRC
+            if new:
+                f.write(self._line({"config": self.config}))
+            f.write(self._line({"unit": list(unit), "res": [[int(x) for x in r] for r in res]}))
+            f.flush()
+            os.fsync(f.fileno())
+
+
+def gpu_unit_runner(texts, samples=256, seed=2, device="cuda"):
+    """Runs one census unit with mk_census on the GPU: the unit's formulas
+    on its layer, frames restricted to its K-index chunk."""
+    def run(unit):
+        p0, p1, c, n, lo, hi = unit
+        job = CensusJob(texts[p0:p1], (c,), n, n, samples=samples, seed=seed, frame_lo=lo, frame_hi=hi,
+                        device=device)
+        return job.run()[:, 0, 0, :]
+    return run
+
+
+def resumable_census(texts, classes, n_min, n_max, directory, runner=None, rank=0, world=1, samples=256, seed=2,
+                     tile=256, frame_chunk=1 << 22, after_unit=None):
+    """Runs this rank's share of the census units (unit i belongs to rank
+    i % world) that no journal in ``directory`` holds yet, recording each
+    as it finishes.  ``runner(unit)`` returns the unit's [formulas][3]
+    results (default: mk_census on the GPU); ``after_unit(unit)`` is called
+    after each recorded unit.  Returns the units run now."""
+    cfg = _journal_config(texts, classes, n_min, n_max, samples, seed, tile, frame_chunk)
+    journal = CensusJournal(directory, rank, cfg)
+    done = journal.finished()
+    runner = runner or gpu_unit_runner(texts, samples, seed)
+    ran = []
+    for i, u in enumerate(census_units(len(texts), classes, n_min, n_max, tile, frame_chunk)):
+        if i % world != rank or u in done:
+            continue
+        res = np.asarray(runner(u), np.uint64)
+        journal.record(u, res)
+        ran.append(u)
+        if after_unit:
+            after_unit(u)
+    return ran
+
+
+def merge_census_journal(texts, classes, n_min, n_max, directory, samples=256, seed=2, tile=256,
+                         frame_chunk=1 << 22):
+    """The census result [formula][class][n - n_min][3] merged from the
+    journals (counts summed, least key); raises if a unit is missing."""
+    cfg = _journal_config(texts, classes, n_min, n_max, samples, seed, tile, frame_chunk)
+    done = CensusJournal(directory, -1, cfg).finished()
+    out = np.zeros((len(texts), len(classes), n_max - n_min + 1, 3), np.uint64)
+    out[..., 2] = np.uint64(mk.NO_KEY)
+    missing = 0
+    for u in census_units(len(texts), classes, n_min, n_max, tile, frame_chunk):
+        if u not in done:
+            missing += 1
+            continue
+        p0, p1, c, n, _, _ = u
+        r = np.asarray(done[u], np.uint64)
+        blk = out[p0:p1, classes.index(c), n - n_min]
+        blk[:, 0] += r[:, 0]
+        blk[:, 1] += r[:, 1]
+        blk[:, 2] = np.minimum(blk[:, 2], r[:, 2])
+    if missing:
+        raise RuntimeError("%d census units have no journal entry yet" % missing)
+    return out

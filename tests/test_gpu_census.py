@@ -242,3 +242,31 @@ def test_matched_single_formula_workload():
     got = tuple(int(x) for x in job2.run()[0, 0, 0])
     r2 = oracle.census(text2, "K", 5, f_lo=0, f_hi=4096)
     assert got == (r2["cm_count"], r2["frames_refuted"], oracle_key(r2))
+
+
+def test_resumable_census_on_the_gpu(tmp_path):
+    """The checkpointed census driver with mk_census as its unit runner: a
+    run stopped by a failure after a few units, then resumed, merges to the
+    one-call census bit for bit, and the resume runs only the missing
+    units."""
+    E = engine()
+    texts = W.census5_formulas()[:40] + list(W.AXIOMS)
+    kw = dict(samples=256, seed=2, tile=16, frame_chunk=1 << 12)
+    d = str(tmp_path / "ckpt")
+    units = E.census_units(len(texts), CLS, 1, 4, kw["tile"], kw["frame_chunk"])
+
+    class Stop(Exception):
+        pass
+
+    def stop_after(u, seen=[]):
+        seen.append(u)
+        if len(seen) == 7:
+            raise Stop()
+
+    with pytest.raises(Stop):
+        E.resumable_census(texts, CLS, 1, 4, d, after_unit=stop_after, **kw)
+    ran = E.resumable_census(texts, CLS, 1, 4, d, **kw)
+    assert len(ran) == len(units) - 7
+    got = E.merge_census_journal(texts, CLS, 1, 4, d, **kw)
+    want = E.CensusJob(texts, CLS, 1, 4, samples=256, seed=2).run()
+    assert np.array_equal(got, want)
