@@ -54,6 +54,10 @@ DRAM_BYTES_PER_PAIR_MLP = (10058240 + 24808704) / 77824
 DRAM_BYTES_PER_RELATION_STRESS = 1339392 / 65536
 # census_queue_kernel<5, 4, 128> on 2,000 uneven-batch formulas: 1.41 MB read
 DRAM_BYTES_PER_FORMULA_UNEVEN = 1411840 / 2000
+# separate_kernel<6> on one 2^27-frame chunk of 64 of the bench's late pairs
+# (ncu capture of the separation6:64 profile case), per pair staged; None
+# until captured
+DRAM_BYTES_PER_PAIR_SEPARATION6 = None
 
 
 def parse():
@@ -69,7 +73,8 @@ def parse():
                          "formulas of the uneven batch, one persistent launch twice; "
                          "census5:F -- run the K n=5 layer of the first F five-world formulas twice "
                          "(a warm-up and the launch an ncu capture selects with -s 1 -c 1), then exit; "
-                         "separation:P -- the same for the first P separation pairs at n=6; "
+                         "separation:P -- the same for the first P separation pairs at n=6; separation6:P -- the "
+                         "first P pairs that agree through five worlds, at n=6 (the bench's dominant kernel); "
                          "stress:P -- the first P mining candidates on 2^16 12-world relations (two "
                          "stress_kernel launches per run: constant pairs, then pairs with a variable)")
     ap.add_argument("--relations", type=int, default=1 << 18,
@@ -202,7 +207,7 @@ def run_mk(args):
     from paper_2606_15437_gb300 import build as mkbuild
     from paper_2606_15437_gb300 import mk
     from paper_2606_15437_gb300 import workloads as W
-    from paper_2606_15437_gb300.engine import lop3_per_eval, n_valuations
+    from paper_2606_15437_gb300.engine import lop3_per_eval, n_valuations, source_ops_per_eval
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -246,13 +251,15 @@ def run_mk(args):
 
     # algorithmic work
     evals = 0
-    ops_dom = 0.0
-    for p in progs:
+    ops_dom = 0.0          # logic ops of the compiled programs (normal form, folded constants)
+    ops_src = 0.0          # logic ops counted on the source formulas
+    for p, text in zip(progs, formulas):
         k = int(p["nvars"])
         for cls in ("K", "T", "S4", "S5"):
             for n in range(1, 6):
                 evals += mk.class_frames(cls, n) * n_valuations(k, n, S)
         ops_dom += (1 << 25) * n_valuations(k, 5, S) * lop3_per_eval(p, 5)
+        ops_src += (1 << 25) * n_valuations(k, 5, S) * source_ops_per_eval(text, 5)
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
@@ -333,6 +340,7 @@ def run_mk(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_tops = sms * LOP3_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
     achieved = ops_dom / (dom_ms / 1e3) / 1e12
+    achieved_src = ops_src / (dom_ms / 1e3) / 1e12
     value = world * evals * args.steps / (ms / 1e3) / 1e9
     e2e_value = world * evals * args.steps / (e2e_ms / 1e3) / 1e9
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -345,6 +353,12 @@ def run_mk(args):
            "roofline": {"bound": "alu", "kernel": "census_layer_kernel<5> (K, n=5)",
                         "achieved": achieved, "peak": peak_tops, "unit": "Tops/s (3-input logic ops)",
                         "frac": achieved / peak_tops, "traffic": DRAM_BYTES_PER_FORMULA_K5 * nprog,
+                        "basis": "compiled programs: (n*#Boolean + n^2*#modal + n)/32 per evaluation, counted "
+                                 "after the negation normal form and constant folding",
+                        "frac_survey": achieved_src / peak_tops, "achieved_survey": achieved_src,
+                        "basis_survey": "source formulas: (n*#Boolean + n^2*#modal + n)/32 per evaluation, "
+                                        "operators counted in the formula text",
+                        "algorithmic_ops_per_launch_survey": ops_src,
                         "traffic_note": "bytes per launch, scaled from a 16-formula ncu capture",
                         "algorithmic_ops_per_launch": ops_dom, "launch_ms": dom_ms,
                         "peak_basis": "%d SMs x %d logic ops/clk x %.0f MHz" % (sms, LOP3_PER_SM_CLK, SM_MAX_MHZ),
@@ -464,10 +478,27 @@ def run_uneven(args):
     print(json.dumps(out), flush=True)
 
 
+def separation_ops(pair, n, progs=None):
+    """Algorithmic logic ops per (pair, frame, valuation) on n worlds:
+    ops(phi) + ops(psi) + n, over 32 frames per word, with ops(phi) =
+    n * #Boolean + n^2 * #modal -- counted on the source formulas, or, given
+    progs = (program of phi, program of psi), on the compiled programs
+    (after the normal form and constant folding)."""
+    if progs is None:
+        from paper_2606_15437_gb300.engine import source_op_counts
+        (ba, ma), (bb, mb) = source_op_counts(pair[0]), source_op_counts(pair[1])
+    else:
+        ba, ma = int(progs[0]["n_bool"]), int(progs[0]["n_modal"])
+        bb, mb = int(progs[1]["n_bool"]), int(progs[1]["n_modal"])
+    return (n * (ba + bb) + n * n * (ma + mb) + n) / 32.0
+
+
 def run_separation(args):
     """Separation search over 1,024 variable-free pairs: every labelled frame
     of 1..6 worlds in K-index order, then 1e8 sampled Erdos-Renyi relations
-    at 7 and 8 worlds for pairs still unsplit; every split re-certified."""
+    at 7 and 8 worlds for pairs still unsplit; every split re-certified.
+    The roofline is taken on the dominant kernel, the six-world exhaustive
+    search, timed alone on exactly the pairs that reach six worlds."""
     import torch
     from paper_2606_15437_gb300 import build as mkbuild
     from paper_2606_15437_gb300 import engine as E
@@ -491,30 +522,119 @@ def run_separation(args):
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     keys = job.results()
-    # evaluations up to each pair's first split (frames before it, and the split frame)
-    evals = 0
+    # evaluations and algorithmic logic ops up to each pair's first split
+    # (the frames before it, and the split frame)
+    evals, ops, ops_c = 0, 0.0, 0.0
     by_n = {}
     certified = 0
+    six, ops6, ops6_c = [], 0.0, 0.0
     for i, key in enumerate(keys):
+        pr = (job.pa[i], job.pb[i])
         key = int(key)
-        sizes = list(range(1, 7)) + [7, 8]
-        if key == mk.NO_KEY:
-            evals += sum((1 << (n * n)) for n in range(1, 7)) + 2 * fpn
-            by_n["none"] = by_n.get("none", 0) + 1
-            continue
-        n, f = mk.split_n(key), (key >> 24) & ((1 << 36) - 1)
-        evals += sum((1 << (m * m)) for m in range(1, min(n, 7))) + (fpn if n == 8 else 0) + f + 1
-        by_n[n] = by_n.get(n, 0) + 1
-        certified += mk.certify_struct(job.certificate(i, key)) == 1
+        n_split = 9 if key == mk.NO_KEY else mk.split_n(key)
+        f = None if key == mk.NO_KEY else (key >> 24) & ((1 << 36) - 1)
+        for n in range(1, min(n_split, 8) + 1):
+            frames = (1 << (n * n)) if n <= 6 else fpn
+            if n == n_split:
+                frames = f + 1
+            evals += frames
+            ops += frames * separation_ops(pairs[i], n)
+            ops_c += frames * separation_ops(pairs[i], n, pr)
+            if n == 6:
+                ops6 += frames * separation_ops(pairs[i], 6)
+                ops6_c += frames * separation_ops(pairs[i], 6, pr)
+        if n_split >= 6:
+            six.append(i)
+        by_n["none" if key == mk.NO_KEY else n_split] = by_n.get("none" if key == mk.NO_KEY else n_split, 0) + 1
+        if key != mk.NO_KEY:
+            certified += mk.certify_struct(job.certificate(i, key)) == 1
+    # the dominant kernel alone: the six-world layer for the pairs that reach it
+    job6 = E.SeparateJob([pairs[i] for i in six], 6, 6, seed=4)
+    job6.launch()
+    torch.cuda.synchronize()
+    e6 = [_events() for _ in range(2)]
+    for a, b in e6:
+        a.record()
+        job6.launch()
+        b.record()
+    torch.cuda.synchronize()
+    ms6 = sum(a.elapsed_time(b) for a, b in e6) / len(e6)
+    keys6 = job6.results()
+    for j, i in enumerate(six):
+        k6 = int(keys6[j])
+        assert (k6 == mk.NO_KEY and (int(keys[i]) == mk.NO_KEY or mk.split_n(int(keys[i])) > 6)) or k6 == int(keys[i])
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tops = sms * LOP3_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    achieved6 = ops6_c / (ms6 / 1e3) / 1e12
+    achieved6_src = ops6 / (ms6 / 1e3) / 1e12
+
+    # e2e through the public API: the pairs' programs copied in from pinned
+    # host memory and the split keys copied out, every step
+    h_pa = torch.from_numpy(job.pa.view(np.uint8).copy()).pin_memory()
+    h_pb = torch.from_numpy(job.pb.view(np.uint8).copy()).pin_memory()
+    h_split = torch.empty(len(pairs), dtype=torch.int64).pin_memory()
+    e2e_steps = min(args.steps, 2)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = _events()
+    e0.record()
+    for _ in range(e2e_steps):
+        job.d_pa.copy_(h_pa, non_blocking=True)
+        job.d_pb.copy_(h_pb, non_blocking=True)
+        job.launch()
+        h_split.copy_(job.d_split, non_blocking=True)
+        stream.synchronize()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    assert np.array_equal(h_split.numpy().view(np.uint64), keys)
+
     out = {"metric": METRIC, "value": evals / (ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded)",
            "config": {"workload": "separation search: 1,024 variable-free pairs (32 context pairs, "
                       "alpha_5/alpha_6, seeded random and mutated pairs); all frames n<=6, then 1e8 "
                       "sampled 7- and 8-world frames", "evals_per_step (to first split)": evals,
-                      "splits_by_n": {str(k): v for k, v in sorted(by_n.items(), key=lambda x: str(x[0]))}},
+                      "splits_by_n": {str(k): v for k, v in sorted(by_n.items(), key=lambda x: str(x[0]))},
+                      "l2": "inputs are the frame indices themselves; nothing re-read from HBM"},
            "certified_splits": certified,
+           "roofline": {"bound": "alu", "kernel": "separate_kernel<6> (the six-world exhaustive layer, timed "
+                        "alone on the %d pairs that reach it)" % len(six),
+                        "achieved": achieved6, "peak": peak_tops, "unit": "Tops/s (3-input logic ops)",
+                        "frac": achieved6 / peak_tops,
+                        "traffic": None if DRAM_BYTES_PER_PAIR_SEPARATION6 is None
+                        else DRAM_BYTES_PER_PAIR_SEPARATION6 * len(six),
+                        "traffic_note": "bytes per launch (one 2^27-frame chunk), scaled by the pairs staged "
+                                        "from an ncu capture of 64 late pairs",
+                        "basis": "compiled programs: (n*(#Boolean + n*#modal) of phi and of psi + n)/32 per "
+                                 "(pair, frame), after the normal form and constant folding; frames counted "
+                                 "up to each pair's first split",
+                        "frac_survey": achieved6_src / peak_tops, "achieved_survey": achieved6_src,
+                        "basis_survey": "the same count on the source formulas (the paper's operators as "
+                                        "written; constant subformulas such as []T count in full)",
+                        "algorithmic_ops_per_launch": ops6_c, "algorithmic_ops_per_launch_survey": ops6,
+                        "launch_ms": ms6,
+                        "peak_basis": "%d SMs x %d logic ops/clk x %.0f MHz" % (sms, LOP3_PER_SM_CLK, SM_MAX_MHZ),
+                        "whole_search_frac": ops_c / (ms / 1e3) / 1e12 / peak_tops,
+                        "whole_search_frac_survey": ops / (ms / 1e3) / 1e12 / peak_tops},
+           "e2e": {"value": evals / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
+                   "h2d_bytes_per_step": h_pa.numel() + h_pb.numel(), "d2h_bytes_per_step": h_split.numel() * 8},
+           "gpu_launches": mk.separate_launches(job.cfg, len(pairs)) * args.steps,
            "clocks": clk}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t0, ev_cpu, units = time.perf_counter(), 0, 0
+        while time.perf_counter() - t0 < args.cpu_seconds:
+            a, b = pairs[six[units % len(six)]]
+            lo = (1 << 22) * (units // len(six))
+            oracle.pair_layer(a, b, 6, f_lo=lo, f_hi=lo + (1 << 18))
+            ev_cpu += 1 << 18
+            units += 1
+        secs = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": ev_cpu / secs / 1e9, "unit": UNIT, "cores": oracle.threads(),
+                               "kind": "oracle",
+                               "sample": "oracle.pair_layer on %d (pair, 2^18 six-world frames) windows of the "
+                                         "pairs that reach six worlds" % units}
     print(json.dumps(out), flush=True)
 
 
@@ -795,6 +915,14 @@ def run_profile_case(spec):
         job = E.CensusJob(W.census5_formulas()[:count], ("K",), 5, 5, samples=S, seed=SEED)
     elif kind == "separation":
         job = E.SeparateJob(W.separation_pairs(4)[:count], 6, 6, frame_lo=0, frame_hi=1 << 30)
+    elif kind == "separation6":
+        # the bench's dominant kernel: the first `count` separation pairs that
+        # agree on every frame of <= 5 worlds, on the first 2^30 six-world frames
+        from paper_2606_15437_gb300 import mk
+        pairs = W.separation_pairs(4)
+        keys = E.SeparateJob(pairs, 1, 5).run()
+        late = [pairs[i] for i in range(len(pairs)) if int(keys[i]) == mk.NO_KEY][:count]
+        job = E.SeparateJob(late, 6, 6, frame_lo=0, frame_hi=1 << 30)
     elif kind == "uneven":
         # the first `count` formulas of the uneven batch, one persistent
         # queue launch per run (units 4, 128 threads, 8/8/4/4 tiles)
@@ -962,8 +1090,9 @@ def run_learned(args):
     4,096-bit truth vectors over seeded pointed models of <= 5 worlds, a
     5,467,766-pair Hamming k-NN universe, an MLP (FP32 training, BF16
     scoring, hidden 256) trained on exact-search labels of a disjoint
-    corpus, compared with random and PCA-10 rankings by certified late
-    splits per 1e12 exact evaluations at an equal budget."""
+    corpus, compared with random, random-among-identical-vector-pairs and
+    PCA-10 rankings by certified late splits per 1e12 exact evaluations at
+    an equal budget."""
     import time
     from paper_2606_15437_gb300 import build as mkbuild
     from paper_2606_15437_gb300 import engine as E
@@ -978,8 +1107,10 @@ def run_learned(args):
                       "budget %.3g exact evaluations per ranking" % r["budget_evals"],
                       "train_pairs": r["train_pairs"], "train_late": r["train_late"],
                       "identical_in_universe": r["identical_in_universe"]},
-           "mlp": r["mlp"], "random": r["random"], "pca10": r["pca10"],
+           "mlp": r["mlp"], "random": r["random"], "random_identical": r["random_identical"], "pca10": r["pca10"],
            "gain_vs_random": r["mlp"]["certified_per_1e12_evals"] / max(1e-9, r["random"]["certified_per_1e12_evals"]),
+           "gain_vs_random_identical": r["mlp"]["certified_per_1e12_evals"] /
+           max(1e-9, r["random_identical"]["certified_per_1e12_evals"]),
            "gain_vs_pca10": r["mlp"]["certified_per_1e12_evals"] / max(1e-9, r["pca10"]["certified_per_1e12_evals"]),
            "seconds": time.time() - t0}
     print(json.dumps(out), flush=True)

@@ -9,12 +9,18 @@
 // global atomicMin merges CTAs.
 //
 // Sizes are launched in increasing n; the K frames of the largest sizes are
-// launched in ascending chunks.  A CTA reads each pair's current key when it
-// stages the pair and drops pairs whose key is already below the least key
-// the CTA could produce (a split at a smaller n, or at an earlier chunk), so
-// work on a pair stops soon after its first split ("done" flags read without
-// any wait).  Sampled sizes (7, 8) generate their relations on the device
-// from the counter-based SplitMix64 stream, 32 samples per frame word.
+// launched in ascending chunks.  Before every launch a one-CTA kernel lists
+// the pairs still without a split below the launch's first frame (ascending
+// pair order, in the caller's workspace), and the launch's tiles are cut
+// from that list only, so no CTA stages a finished pair; CTAs whose tile
+// lies past the list's end exit at once.  A CTA stages its tile once and
+// walks a strip of several frame-word groups, dropping a pair for the rest
+// of the strip once the CTA has found its split, and at staging it also
+// drops pairs whose key is already below the least key it could produce
+// (another CTA of the same chunk got there first): work on a pair stops soon
+// after its first split, without any wait.  Sampled sizes (7, 8) generate
+// their relations on the device from the counter-based SplitMix64 stream,
+// 32 samples per frame word.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -42,6 +48,9 @@ struct SepArgs {
     uint64_t nframes;          // frames (K) or samples of this size
     uint64_t f_lo, f_hi;       // K-index filter (exhaustive sizes)
     int32_t full_range;
+    int32_t groups;            // frame-word groups (BLOCK * U words each) per CTA
+    const int32_t *nactive;    // pairs listed in active[] for this launch
+    const int32_t *active;     // pair indices, ascending
     uint64_t *split;
     int32_t *status;
 };
@@ -82,6 +91,33 @@ __device__ __forceinline__ uint32_t sampled_frame_word(uint64_t state, uint64_t 
     return valid;
 }
 
+// Edge words and valid lanes of frame word `word` of this launch.
+template <int N>
+__device__ __forceinline__ uint32_t sep_frame_word(const SepArgs &a, uint64_t word, uint32_t (&E)[N * N]) {
+    const uint64_t base = word << 5;
+    uint32_t valid = 0;
+    if (word < a.word_hi) {
+        if (a.sampled) {
+            valid = sampled_frame_word<N>(a.rel_state, base, a.nframes, E);
+        } else {
+            if constexpr (N <= MK_MAX_WORLDS_EXH) k_frame_word<N>(word, E);
+            if (base < a.nframes) {
+                const uint64_t left = a.nframes - base;
+                valid = left >= 32 ? 0xFFFFFFFFu : ((1u << left) - 1u);
+            }
+            if (!a.full_range) {
+                for (int l = 0; l < 32; ++l)
+                    if (base + l < a.f_lo || base + l >= a.f_hi) valid &= ~(1u << l);
+            }
+        }
+    }
+    if (!valid) {
+#pragma unroll
+        for (int e = 0; e < N * N; ++e) E[e] = 0;
+    }
+    return valid;
+}
+
 template <int N, int U, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
     using SM = SepSmem<N, U, BLOCK>;
@@ -89,26 +125,32 @@ __global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int s_active;
     const int tile = a.tile;
+    // this CTA's tile of the active-pair list (uniform: one load of the count)
+    const int na_list = *a.nactive;
+    const int t0 = blockIdx.y * tile;
+    if (t0 >= na_list) return;
+    const int np = min(tile, na_list - t0);
     uint16_t *s_offs_a = (uint16_t *)smem;
     uint16_t *s_offs_b = s_offs_a + (size_t)tile * SEP_OPS_STRIDE;
     uint8_t *s_ops_a = (uint8_t *)(s_offs_b + (size_t)tile * SEP_OPS_STRIDE);
     uint8_t *s_ops_b = s_ops_a + (size_t)tile * SEP_OPS_STRIDE;
     int *s_na = (int *)(smem + SM::code_bytes(tile));
-    int *s_nb = s_na + tile;
-    int *s_k = s_nb + tile;
+    int *s_pair = s_na + tile;
+    int *s_k = s_pair + tile;
     int *s_pad = s_k + tile;
     unsigned long long *s_key = (unsigned long long *)(s_pad + tile);
     uint32_t *s_rows = (uint32_t *)(smem + SM::code_bytes(tile) + SM::meta_bytes(tile));
     uint32_t *s_stack = (uint32_t *)((uint8_t *)s_rows + SM::row_bytes()) + threadIdx.x;
 
-    const uint64_t cta_word0 = a.word_lo + (uint64_t)blockIdx.x * BLOCK * U;
+    const uint64_t strip_words = (uint64_t)BLOCK * U;
+    const uint64_t cta_word0 = a.word_lo + (uint64_t)blockIdx.x * a.groups * strip_words;
+    if (cta_word0 >= a.word_hi) return;
     const unsigned long long floor_key = split_key(a.sampled, N, cta_word0 << 5, 0, 0);
     if (threadIdx.x == 0) s_active = 0;
     __syncthreads();
-    const int p0 = blockIdx.y * tile;
-    const int np = min(tile, a.npairs - p0);
     for (int i = threadIdx.x; i < np; i += BLOCK) {
-        const mk_program &pa = a.phi[p0 + i], &pb = a.psi[p0 + i];
+        const int pi = a.active[t0 + i];
+        const mk_program &pa = a.phi[pi], &pb = a.psi[pi];
         int ok = program_ok(pa) && program_ok(pb);
         if (!ok && blockIdx.x == 0) atomicOr(a.status, (int)MK_ST_PROGRAM);
         const int k = pa.nvars > pb.nvars ? pa.nvars : pb.nvars;
@@ -119,9 +161,9 @@ __global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
             if (blockIdx.x == 0) atomicOr(a.status, (int)MK_ST_LIMIT);
         }
         // a split already below this CTA's least key ends the pair here
-        if (ok && ((volatile unsigned long long *)a.split)[p0 + i] < floor_key) ok = 0;
+        if (ok && ((volatile unsigned long long *)a.split)[pi] < floor_key) ok = 0;
         s_na[i] = ok ? pa.n_instr : -1;
-        s_nb[i] = pb.n_instr;
+        s_pair[i] = pi;
         s_k[i] = k;
         s_key[i] = ~0ull;
         if (ok) {
@@ -133,105 +175,126 @@ __global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
     __syncthreads();
     if (s_active == 0) return;
 
-    uint32_t E[U][N * N];
-    uint32_t valid[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const uint64_t word = cta_word0 + (uint64_t)threadIdx.x * U + u;
-        const uint64_t base = word << 5;
-        valid[u] = 0;
-        if (word < a.word_hi) {
-            if (a.sampled) {
-                valid[u] = sampled_frame_word<N>(a.rel_state, base, a.nframes, E[u]);
-            } else {
-                if constexpr (N <= MK_MAX_WORLDS_EXH) k_frame_word<N>(word, E[u]);
-                if (base < a.nframes) {
-                    const uint64_t left = a.nframes - base;
-                    valid[u] = left >= 32 ? 0xFFFFFFFFu : ((1u << left) - 1u);
-                }
-                if (!a.full_range) {
-                    for (int l = 0; l < 32; ++l)
-                        if (base + l < a.f_lo || base + l >= a.f_hi) valid[u] &= ~(1u << l);
-                }
-            }
-        }
-        if (!valid[u]) {
-#pragma unroll
-            for (int e = 0; e < N * N; ++e) E[u][e] = 0;
-        }
-    }
     const int lane = threadIdx.x & 31;
     int rows_kind = -1;
     uint32_t rows_c0 = 0;
-    __syncthreads();
-
-    for (int fi = 0; fi < np; ++fi) {
-        const int na = s_na[fi];
-        if (na < 0) continue;
-        const int nb = s_nb[fi];
-        const int k = s_k[fi];
-        const bool exh = exhaustive_vals(k, N, a.S);
-        const uint32_t nval = exh ? (1u << (k * N)) : a.S;
-        const uint8_t *oa = s_ops_a + fi * SEP_OPS_STRIDE, *ob = s_ops_b + fi * SEP_OPS_STRIDE;
-        const uint16_t *fa = s_offs_a + fi * SEP_OPS_STRIDE, *fb = s_offs_b + fi * SEP_OPS_STRIDE;
-        int best_o = U * 32, best_w = 0;     // o = u * 32 + lane: ascending frames
-        uint32_t best_j = 0;
-        for (uint32_t c0 = 0; c0 < nval; c0 += SEP_ROW_CAP) {
-            const uint32_t cn = min((uint32_t)SEP_ROW_CAP, nval - c0);
-            if (rows_kind != (exh ? 0 : 1) || rows_c0 != c0) {
-                __syncthreads();
-                constexpr int W = RowShape<N>::WORDS;
-                const uint32_t rows = exh ? (uint32_t)SEP_ROW_CAP : min((uint32_t)SEP_ROW_CAP, a.S - c0);
-                for (uint32_t i = threadIdx.x; i < rows * W; i += BLOCK) {
-                    const uint32_t j = c0 + i / W;
-                    s_rows[i] = atom_row_word<N>(exh ? j : a.samples[j], (int)(i % W));
+    for (int g = 0; g < a.groups; ++g) {
+        const uint64_t gw0 = cta_word0 + (uint64_t)g * strip_words;
+        if (gw0 >= a.word_hi) break;                       // uniform
+        uint32_t E[U][N * N];
+        uint32_t valid[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) valid[u] = sep_frame_word<N>(a, gw0 + (uint64_t)threadIdx.x * U + u, E[u]);
+        // pairs whose split this CTA found in an earlier group: read by every
+        // thread before any thread can write s_key again, so the skips below
+        // (and the barriers of row staging) are uniform across the CTA
+        uint64_t found = 0;
+        for (int fi = 0; fi < np; ++fi)
+            if (s_key[fi] != ~0ull) found |= 1ull << fi;
+        __syncthreads();
+        for (int fi = 0; fi < np; ++fi) {
+            if (s_na[fi] < 0 || ((found >> fi) & 1ull)) continue;   // finished pair, or split found here
+            const int k = s_k[fi];
+            const bool exh = exhaustive_vals(k, N, a.S);
+            const uint32_t nval = exh ? (1u << (k * N)) : a.S;
+            const uint8_t *oa = s_ops_a + fi * SEP_OPS_STRIDE, *ob = s_ops_b + fi * SEP_OPS_STRIDE;
+            const uint16_t *fa = s_offs_a + fi * SEP_OPS_STRIDE, *fb = s_offs_b + fi * SEP_OPS_STRIDE;
+            int best_o = U * 32, best_w = 0;     // o = u * 32 + lane: ascending frames
+            uint32_t best_j = 0;
+            for (uint32_t c0 = 0; c0 < nval; c0 += SEP_ROW_CAP) {
+                const uint32_t cn = min((uint32_t)SEP_ROW_CAP, nval - c0);
+                if (rows_kind != (exh ? 0 : 1) || rows_c0 != c0) {
+                    __syncthreads();
+                    constexpr int W = RowShape<N>::WORDS;
+                    const uint32_t rows = exh ? (uint32_t)SEP_ROW_CAP : min((uint32_t)SEP_ROW_CAP, a.S - c0);
+                    for (uint32_t i = threadIdx.x; i < rows * W; i += BLOCK) {
+                        const uint32_t j = c0 + i / W;
+                        s_rows[i] = atom_row_word<N>(exh ? j : a.samples[j], (int)(i % W));
+                    }
+                    __syncthreads();
+                    rows_kind = exh ? 0 : 1;
+                    rows_c0 = c0;
                 }
-                __syncthreads();
-                rows_kind = exh ? 0 : 1;
-                rows_c0 = c0;
-            }
-            for (uint32_t jj = 0; jj < cn && best_o > 0; ++jj) {
-                uint32_t A[U][N], B[U][N];
-                run_program<N, U, U, BLOCK, 0, false>(oa, fa, s_rows + jj * RW, E, s_stack, A);
-                run_program<N, U, U, BLOCK, 0, false>(ob, fb, s_rows + jj * RW, E, s_stack, B);
+                for (uint32_t jj = 0; jj < cn && best_o > 0; ++jj) {
+                    uint32_t A[U][N], B[U][N];
+                    run_program<N, U, U, BLOCK, 0, false>(oa, fa, s_rows + jj * RW, E, s_stack, A);
+                    run_program<N, U, U, BLOCK, 0, false>(ob, fb, s_rows + jj * RW, E, s_stack, B);
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    uint32_t any = 0;
+                    for (int u = 0; u < U; ++u) {
+                        uint32_t any = 0;
 #pragma unroll
-                    for (int w = 0; w < N; ++w) any |= A[u][w] ^ B[u][w];
-                    any &= valid[u];
-                    if (any) {
-                        const int o = u * 32 + __ffs(any) - 1;
-                        if (o < best_o) {
-                            const int l = o - u * 32;
-                            best_o = o;
-                            best_j = c0 + jj;
-                            int bw = 0;
+                        for (int w = 0; w < N; ++w) any |= A[u][w] ^ B[u][w];
+                        any &= valid[u];
+                        if (any) {
+                            const int o = u * 32 + __ffs(any) - 1;
+                            if (o < best_o) {
+                                const int l = o - u * 32;
+                                best_o = o;
+                                best_j = c0 + jj;
+                                int bw = 0;
 #pragma unroll
-                            for (int w = N - 1; w >= 0; --w)
-                                if (((A[u][w] ^ B[u][w]) >> l) & 1u) bw = w;
-                            best_w = bw;
+                                for (int w = N - 1; w >= 0; --w)
+                                    if (((A[u][w] ^ B[u][w]) >> l) & 1u) bw = w;
+                                best_w = bw;
+                            }
                         }
                     }
                 }
             }
-        }
-        const uint32_t hit = __ballot_sync(0xFFFFFFFFu, best_o < U * 32);
-        if (hit) {
-            // threads hold ascending frame words, so the lowest hit lane wins
-            const int src_lane = __ffs(hit) - 1;
-            uint64_t my = 0;
-            if (lane == src_lane) {
-                const uint64_t f = ((cta_word0 + (uint64_t)threadIdx.x * U) << 5) + (uint64_t)best_o;
-                my = split_key(a.sampled, N, f, best_j, (uint64_t)best_w);
+            const uint32_t hit = __ballot_sync(0xFFFFFFFFu, best_o < U * 32);
+            if (hit) {
+                // threads hold ascending frame words, so the lowest hit lane wins
+                const int src_lane = __ffs(hit) - 1;
+                uint64_t my = 0;
+                if (lane == src_lane) {
+                    const uint64_t f = ((gw0 + (uint64_t)threadIdx.x * U) << 5) + (uint64_t)best_o;
+                    my = split_key(a.sampled, N, f, best_j, (uint64_t)best_w);
+                }
+                const uint64_t key = __shfl_sync(0xFFFFFFFFu, my, src_lane);
+                if (lane == 0) atomicMin(&s_key[fi], (unsigned long long)key);
             }
-            const uint64_t key = __shfl_sync(0xFFFFFFFFu, my, src_lane);
-            if (lane == 0) atomicMin(&s_key[fi], (unsigned long long)key);
         }
+        __syncthreads();
     }
-    __syncthreads();
     for (int i = threadIdx.x; i < np; i += BLOCK)
-        if (s_key[i] != ~0ull) atomicMin((unsigned long long *)&a.split[p0 + i], s_key[i]);
+        if (s_key[i] != ~0ull) atomicMin((unsigned long long *)&a.split[s_pair[i]], s_key[i]);
+}
+
+// The pairs of split[] whose key is not below floor_key (no split found
+// before the next launch's first frame), in ascending order: one CTA of
+// SEP_LIST_THREADS threads, a ballot-and-scan compaction per 1,024 pairs.
+constexpr int SEP_LIST_THREADS = 1024;
+__global__ void __launch_bounds__(SEP_LIST_THREADS) active_pairs_kernel(const uint64_t *split, int npairs,
+                                                                        uint64_t floor_key, int32_t *nactive,
+                                                                        int32_t *active) {
+    __shared__ int s_warp[SEP_LIST_THREADS / 32];
+    __shared__ int s_base;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_base = 0;
+    __syncthreads();
+    for (int b = 0; b < npairs; b += SEP_LIST_THREADS) {
+        const int i = b + threadIdx.x;
+        const bool act = i < npairs && split[i] >= floor_key;
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, act);
+        if (lane == 0) s_warp[warp] = __popc(m);
+        __syncthreads();
+        if (warp == 0) {
+            const int v = s_warp[lane];
+            int inc = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                if (lane >= o) inc += t;
+            }
+            s_warp[lane] = inc - v;                         // exclusive offset of each warp
+        }
+        __syncthreads();
+        if (act) active[s_base + s_warp[warp] + __popc(m & ((1u << lane) - 1u))] = i;
+        __syncthreads();
+        if (threadIdx.x == SEP_LIST_THREADS - 1) s_base += s_warp[warp] + __popc(m);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *nactive = s_base;
 }
 
 __global__ void init_split_kernel(uint64_t *split, int n) {
@@ -249,16 +312,29 @@ constexpr int SEP_BLOCK = 256;
 template <int N>
 constexpr int sep_units() { return N <= 6 ? 2 : 1; }
 
+// CTAs per launch below which a strip holds a single group: four waves of
+// two CTAs on 152 SMs, so that even a single active tile fills the GPU.
+constexpr uint64_t SEP_MIN_CTAS = 1216;
+constexpr uint64_t SEP_MAX_GROUPS = 8;
+
 template <int N>
-void launch_sep(const SepArgs &a, cudaStream_t s) {
+void launch_sep(SepArgs a, cudaStream_t s) {
     constexpr int U = sep_units<N>();
     const uint64_t words = a.word_hi > a.word_lo ? a.word_hi - a.word_lo : 0;
     if (words == 0 || a.npairs == 0) return;
-    const uint64_t per_cta = (uint64_t)SEP_BLOCK * U;
-    dim3 grid((unsigned)((words + per_cta - 1) / per_cta), (unsigned)((a.npairs + a.tile - 1) / a.tile));
+    const uint64_t per_group = (uint64_t)SEP_BLOCK * U;
+    const uint64_t groups = (words + per_group - 1) / per_group;
+    uint64_t g = groups / SEP_MIN_CTAS;
+    g = g < 1 ? 1 : (g > SEP_MAX_GROUPS ? SEP_MAX_GROUPS : g);
+    a.groups = (int32_t)g;
+    dim3 grid((unsigned)((groups + g - 1) / g), (unsigned)((a.npairs + a.tile - 1) / a.tile));
     const size_t sm = SepSmem<N, U, SEP_BLOCK>::total(a.tile);
     auto kern = separate_kernel<N, U, SEP_BLOCK>;
     ensure_dynamic_smem((const void *)kern, sm);
+    // the pairs without a split below this launch's first frame
+    const uint64_t floor_key = split_key(a.sampled, N, a.word_lo << 5, 0, 0);
+    active_pairs_kernel<<<1, SEP_LIST_THREADS, 0, s>>>(a.split, a.npairs, floor_key, (int32_t *)a.nactive,
+                                                       (int32_t *)a.active);
     kern<<<grid, SEP_BLOCK, sm, s>>>(a);
 }
 
@@ -295,10 +371,11 @@ int check_sep(const mk_separate_cfg *cfg, int32_t npairs) {
 
 }  // namespace
 
+// Workspace: the active-pair count (16 bytes) and the active-pair list.
 extern "C" size_t mk_separate_workspace_size(const mk_separate_cfg *cfg, int32_t npairs) {
     (void)cfg;
-    (void)npairs;
-    return 0;
+    if (npairs <= 0) return 0;
+    return ((size_t)npairs * 4 + 16 + 255) & ~(size_t)255;
 }
 
 extern "C" uint64_t mk_sample_relation(uint64_t seed, int32_t n, uint64_t s) {
@@ -306,30 +383,15 @@ extern "C" uint64_t mk_sample_relation(uint64_t seed, int32_t n, uint64_t s) {
     return sample_relation(sm_stream(seed, 2, (uint64_t)n), n, s);
 }
 
-extern "C" int mk_separate(const mk_program *d_phi, const mk_program *d_psi, int32_t npairs,
-                           const mk_separate_cfg *cfg, uint64_t *d_split, int32_t *d_status,
-                           void *d_workspace, size_t ws_bytes, void *stream) {
-    (void)d_workspace;
-    (void)ws_bytes;
-    int rc = check_sep(cfg, npairs);
-    if (rc != MK_OK) return rc;
-    if (npairs > 0 && (!d_phi || !d_psi || !d_split)) return MK_E_ARG;
-    if (!d_status) return MK_E_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
-    if (npairs == 0) return MK_OK;
-    init_split_kernel<<<(npairs + 255) / 256, 256, 0, s>>>(d_split, npairs);
-    const int tile = cfg->tune.tile ? cfg->tune.tile : 16;
-    const uint64_t chunk_words = 1ull << 22;
+namespace {
 
-    SepArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.phi = d_phi;
-    a.psi = d_psi;
-    a.npairs = npairs;
-    a.tile = tile;
-    a.S = cfg->samples;
-    a.split = d_split;
-    a.status = d_status;
+// Walks the launches of a search in order: every size, and within a size
+// its chunks of frame words.  With a non-null stream pointer it launches
+// them; it returns the number of kernel launches either way.
+int64_t separate_walk(const mk_separate_cfg *cfg, SepArgs &a, const cudaStream_t *s) {
+    const uint64_t chunk_words = 1ull << 22;   // exhaustive sizes: 2^27 frames per launch
+    const uint64_t sampled_words = 1ull << 18; // sampled sizes: 2^23 relations per launch
+    int64_t launches = 1;                       // the split keys' initialisation
     if (cfg->n_exh_max) {
         for (int n = cfg->n_exh_min; n <= cfg->n_exh_max; ++n) {
             const uint64_t kf = 1ull << (n * n);
@@ -344,7 +406,8 @@ extern "C" int mk_separate(const mk_program *d_phi, const mk_program *d_psi, int
             for (uint64_t w = w0; w < w1; w += chunk_words) {
                 a.word_lo = w;
                 a.word_hi = w + chunk_words < w1 ? w + chunk_words : w1;
-                launch_sep_n(n, a, s);
+                if (s) launch_sep_n(n, a, *s);
+                launches += 2;                  // the active-pair list, then the search
             }
         }
     }
@@ -356,14 +419,52 @@ extern "C" int mk_separate(const mk_program *d_phi, const mk_program *d_psi, int
             a.nframes = cfg->frames_per_n;
             a.full_range = 1;
             const uint64_t w1 = (cfg->frames_per_n + 31) / 32;
-            const uint64_t cw = 1ull << 18;
-            for (uint64_t w = 0; w < w1; w += cw) {
+            for (uint64_t w = 0; w < w1; w += sampled_words) {
                 a.word_lo = w;
-                a.word_hi = w + cw < w1 ? w + cw : w1;
-                launch_sep_n(n, a, s);
+                a.word_hi = w + sampled_words < w1 ? w + sampled_words : w1;
+                if (s) launch_sep_n(n, a, *s);
+                launches += 2;
             }
         }
     }
+    return launches;
+}
+
+}  // namespace
+
+extern "C" int64_t mk_separate_launches(const mk_separate_cfg *cfg, int32_t npairs) {
+    if (check_sep(cfg, npairs) != MK_OK) return -1;
+    if (npairs == 0) return 0;
+    SepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    return separate_walk(cfg, a, nullptr);
+}
+
+extern "C" int mk_separate(const mk_program *d_phi, const mk_program *d_psi, int32_t npairs,
+                           const mk_separate_cfg *cfg, uint64_t *d_split, int32_t *d_status,
+                           void *d_workspace, size_t ws_bytes, void *stream) {
+    int rc = check_sep(cfg, npairs);
+    if (rc != MK_OK) return rc;
+    if (npairs > 0 && (!d_phi || !d_psi || !d_split)) return MK_E_ARG;
+    if (!d_status) return MK_E_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (npairs == 0) return MK_OK;
+    if (ws_bytes < mk_separate_workspace_size(cfg, npairs)) return MK_E_WORKSPACE;
+    if (!d_workspace || ((uintptr_t)d_workspace & 15)) return MK_E_ARG;
+    init_split_kernel<<<(npairs + 255) / 256, 256, 0, s>>>(d_split, npairs);
+
+    SepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.phi = d_phi;
+    a.psi = d_psi;
+    a.npairs = npairs;
+    a.tile = cfg->tune.tile ? cfg->tune.tile : 16;
+    a.S = cfg->samples;
+    a.split = d_split;
+    a.status = d_status;
+    a.nactive = (const int32_t *)d_workspace;
+    a.active = (const int32_t *)((uint8_t *)d_workspace + 16);
+    separate_walk(cfg, a, &s);
     return cudaGetLastError() == cudaSuccess ? MK_OK : MK_E_CUDA;
 }
 
