@@ -230,16 +230,8 @@ def run_mk(args):
 
     # one step = three census calls: the dominant K n=5 layer alone (timed
     # by its own events), K n=1..4, and T/S4/S5 n=1..5
-    parts = [((mk.CLASS_BITS["K"]), 5, 5), ((mk.CLASS_BITS["K"]), 1, 4),
-             (mk.CLASS_BITS["T"] | mk.CLASS_BITS["S4"] | mk.CLASS_BITS["S5"], 1, 5)]
-    calls = []
-    for cls, lo, hi in parts:
-        cfg = mk.census_cfg(cls, lo, hi, S, d_samples.data_ptr(), max_depth=max(1, int(progs["depth"].max())))
-        ws = mk.census_workspace_size(cfg, nprog)
-        ncls = bin(cls).count("1")
-        out = torch.empty(nprog * ncls * (hi - lo + 1) * 3, dtype=torch.int64, device=dev)
-        calls.append({"cfg": cfg, "ws": torch.empty(max(ws, 1), dtype=torch.uint8, device=dev),
-                      "ws_bytes": ws, "out": out, "launches": mk.census_launches(cfg, nprog)})
+    from paper_2606_15437_gb300.engine import census_call_plan
+    calls = census_call_plan(progs, S, d_samples.data_ptr(), dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
@@ -507,8 +499,8 @@ def run_separation(args):
     mkbuild.build()
     dev = torch.device("cuda", 0)
     pairs = W.separation_pairs(4)
-    fpn = 100_000_000
-    job = E.SeparateJob(pairs, 1, 6, 7, 8, frames_per_n=fpn, seed=4)
+    fpn = E.SEPARATION_SEARCH["frames_per_n"]
+    job = E.SeparateJob(pairs, **E.SEPARATION_SEARCH)
     for _ in range(args.warmup):
         job.launch()
     torch.cuda.synchronize()

@@ -323,6 +323,9 @@ typedef struct {
     uint64_t seed;                 /* seed of the relation stream               */
     uint64_t frame_lo, frame_hi;   /* K-index range of exhaustive sizes         */
     mk_tune tune;
+    uint8_t max_depth;             /* largest program depth among phi and psi   */
+                                   /* (0 = MK_MAX_STACK); a deeper program sets */
+                                   /* MK_ST_PROGRAM and its pair is skipped      */
 } mk_separate_cfg;
 
 /* Distinguishing-pair search (Def. 2, Prop. 4): for each pair i, the least

@@ -49,6 +49,7 @@ struct SepArgs {
     uint64_t f_lo, f_hi;       // K-index filter (exhaustive sizes)
     int32_t full_range;
     int32_t groups;            // frame-word groups (BLOCK * U words each) per CTA
+    int32_t depth;             // stack entries provided (the batch's largest program depth)
     const int32_t *nactive;    // pairs listed in active[] for this launch
     const int32_t *active;     // pair indices, ascending
     uint64_t *split;
@@ -62,8 +63,10 @@ struct SepSmem {
     // 16-byte aligned (they are read with 16-byte loads)
     static constexpr size_t meta_bytes(int tile) { return ((size_t)tile * 24 + 15) & ~(size_t)15; }
     static constexpr size_t row_bytes() { return (size_t)SEP_ROW_CAP * RowShape<N>::WORDS * 4; }
-    static constexpr size_t stack_bytes() { return (size_t)MK_MAX_STACK * U * N * BLOCK * 4; }
-    static size_t total(int tile) { return code_bytes(tile) + meta_bytes(tile) + row_bytes() + stack_bytes(); }
+    static constexpr size_t stack_bytes(int depth) { return (size_t)depth * U * N * BLOCK * 4; }
+    static size_t total(int tile, int depth) {
+        return code_bytes(tile) + meta_bytes(tile) + row_bytes() + stack_bytes(depth);
+    }
 };
 
 // Edge words of 32 sampled relations s = base .. base+31 (lane l <- s).
@@ -91,34 +94,46 @@ __device__ __forceinline__ uint32_t sampled_frame_word(uint64_t state, uint64_t 
     return valid;
 }
 
-// Edge words and valid lanes of frame word `word` of this launch.
-template <int N>
-__device__ __forceinline__ uint32_t sep_frame_word(const SepArgs &a, uint64_t word, uint32_t (&E)[N * N]) {
+// Valid lanes of frame word `word` of this launch (frames that exist and,
+// for a K-index window, lie inside it).
+__device__ __forceinline__ uint32_t sep_valid_lanes(const SepArgs &a, uint64_t word) {
     const uint64_t base = word << 5;
-    uint32_t valid = 0;
-    if (word < a.word_hi) {
-        if (a.sampled) {
-            valid = sampled_frame_word<N>(a.rel_state, base, a.nframes, E);
-        } else {
-            if constexpr (N <= MK_MAX_WORLDS_EXH) k_frame_word<N>(word, E);
-            if (base < a.nframes) {
-                const uint64_t left = a.nframes - base;
-                valid = left >= 32 ? 0xFFFFFFFFu : ((1u << left) - 1u);
-            }
-            if (!a.full_range) {
-                for (int l = 0; l < 32; ++l)
-                    if (base + l < a.f_lo || base + l >= a.f_hi) valid &= ~(1u << l);
-            }
-        }
-    }
-    if (!valid) {
-#pragma unroll
-        for (int e = 0; e < N * N; ++e) E[e] = 0;
+    if (word >= a.word_hi || base >= a.nframes) return 0;
+    const uint64_t left = a.nframes - base;
+    uint32_t valid = left >= 32 ? 0xFFFFFFFFu : ((1u << left) - 1u);
+    if (!a.sampled && !a.full_range) {
+        for (int l = 0; l < 32; ++l)
+            if (base + l < a.f_lo || base + l >= a.f_hi) valid &= ~(1u << l);
     }
     return valid;
 }
 
-template <int N, int U, int BLOCK>
+// log2 of the unit count (U a power of two <= 8)
+template <int U>
+constexpr int ulog2() { return U >= 8 ? 3 : U >= 4 ? 2 : U >= 2 ? 1 : 0; }
+
+// Edge words of the U consecutive K frame words w0, w0+1, ... (w0 a multiple
+// of U).  Frame f = 32*word + lane has edge bit e = bit e of f: bits 0-4 are
+// the lane patterns, bits 5 .. 5+log2(U)-1 are the bits of the unit u (all
+// ones or all zeros, known at compile time once u and e are), and every
+// higher bit is the same for all U words.  Written per unit, the identical
+// words collapse to one register and the constant ones into the logic ops.
+template <int N, int U>
+__device__ __forceinline__ void k_unit_words(uint64_t w0, uint32_t (&E)[U][N * N]) {
+    constexpr int LU = ulog2<U>();
+    const uint64_t base = w0 << 5;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int e = 0; e < N * N; ++e)
+            E[u][e] = e < 5 ? lane_pattern(e)
+                    : e < 5 + LU ? (((u >> (e - 5)) & 1) ? 0xFFFFFFFFu : 0u)
+                    : bit_word(base, e);
+}
+
+// SAMPLED: frames are sampled relations (edge words built per unit);
+// otherwise K frames, U consecutive words per thread (k_unit_words).
+template <int N, int U, int BLOCK, bool SAMPLED>
 __global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
     using SM = SepSmem<N, U, BLOCK>;
     constexpr int RW = RowShape<N>::WORDS;
@@ -151,7 +166,7 @@ __global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
     for (int i = threadIdx.x; i < np; i += BLOCK) {
         const int pi = a.active[t0 + i];
         const mk_program &pa = a.phi[pi], &pb = a.psi[pi];
-        int ok = program_ok(pa) && program_ok(pb);
+        int ok = program_ok(pa) && program_ok(pb) && pa.depth <= a.depth && pb.depth <= a.depth;
         if (!ok && blockIdx.x == 0) atomicOr(a.status, (int)MK_ST_PROGRAM);
         const int k = pa.nvars > pb.nvars ? pa.nvars : pb.nvars;
         const bool exh = exhaustive_vals(k, N, a.S);
@@ -183,8 +198,23 @@ __global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
         if (gw0 >= a.word_hi) break;                       // uniform
         uint32_t E[U][N * N];
         uint32_t valid[U];
+        const uint64_t tw0 = gw0 + (uint64_t)threadIdx.x * U;
+        if constexpr (SAMPLED) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) valid[u] = sep_frame_word<N>(a, gw0 + (uint64_t)threadIdx.x * U + u, E[u]);
+            for (int u = 0; u < U; ++u) {
+                valid[u] = sep_valid_lanes(a, tw0 + u);
+                if (valid[u]) {
+                    sampled_frame_word<N>(a.rel_state, (tw0 + u) << 5, a.nframes, E[u]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < N * N; ++e) E[u][e] = 0;
+                }
+            }
+        } else {
+            k_unit_words<N, U>(tw0, E);
+#pragma unroll
+            for (int u = 0; u < U; ++u) valid[u] = sep_valid_lanes(a, tw0 + u);
+        }
         // pairs whose split this CTA found in an earlier group: read by every
         // thread before any thread can write s_key again, so the skips below
         // (and the barriers of row staging) are uniform across the CTA
@@ -309,17 +339,19 @@ using namespace mkd;
 
 constexpr int SEP_BLOCK = 256;
 
-template <int N>
-constexpr int sep_units() { return N <= 6 ? 2 : 1; }
+// Frame words per thread: K frames share their edge words across units
+// (k_unit_words), sampled relations need a full set per unit.
+template <int N, bool SAMPLED>
+constexpr int sep_units() { return SAMPLED ? (N <= 6 ? 2 : 1) : 4; }
 
 // CTAs per launch below which a strip holds a single group: four waves of
 // two CTAs on 152 SMs, so that even a single active tile fills the GPU.
 constexpr uint64_t SEP_MIN_CTAS = 1216;
 constexpr uint64_t SEP_MAX_GROUPS = 8;
 
-template <int N>
+template <int N, bool SAMPLED>
 void launch_sep(SepArgs a, cudaStream_t s) {
-    constexpr int U = sep_units<N>();
+    constexpr int U = sep_units<N, SAMPLED>();
     const uint64_t words = a.word_hi > a.word_lo ? a.word_hi - a.word_lo : 0;
     if (words == 0 || a.npairs == 0) return;
     const uint64_t per_group = (uint64_t)SEP_BLOCK * U;
@@ -328,8 +360,8 @@ void launch_sep(SepArgs a, cudaStream_t s) {
     g = g < 1 ? 1 : (g > SEP_MAX_GROUPS ? SEP_MAX_GROUPS : g);
     a.groups = (int32_t)g;
     dim3 grid((unsigned)((groups + g - 1) / g), (unsigned)((a.npairs + a.tile - 1) / a.tile));
-    const size_t sm = SepSmem<N, U, SEP_BLOCK>::total(a.tile);
-    auto kern = separate_kernel<N, U, SEP_BLOCK>;
+    const size_t sm = SepSmem<N, U, SEP_BLOCK>::total(a.tile, a.depth);
+    auto kern = separate_kernel<N, U, SEP_BLOCK, SAMPLED>;
     ensure_dynamic_smem((const void *)kern, sm);
     // the pairs without a split below this launch's first frame
     const uint64_t floor_key = split_key(a.sampled, N, a.word_lo << 5, 0, 0);
@@ -339,15 +371,26 @@ void launch_sep(SepArgs a, cudaStream_t s) {
 }
 
 void launch_sep_n(int n, const SepArgs &a, cudaStream_t s) {
-    switch (n) {
-    case 1: launch_sep<1>(a, s); break;
-    case 2: launch_sep<2>(a, s); break;
-    case 3: launch_sep<3>(a, s); break;
-    case 4: launch_sep<4>(a, s); break;
-    case 5: launch_sep<5>(a, s); break;
-    case 6: launch_sep<6>(a, s); break;
-    case 7: launch_sep<7>(a, s); break;
-    case 8: launch_sep<8>(a, s); break;
+    if (a.sampled) {
+        switch (n) {
+        case 1: launch_sep<1, true>(a, s); break;
+        case 2: launch_sep<2, true>(a, s); break;
+        case 3: launch_sep<3, true>(a, s); break;
+        case 4: launch_sep<4, true>(a, s); break;
+        case 5: launch_sep<5, true>(a, s); break;
+        case 6: launch_sep<6, true>(a, s); break;
+        case 7: launch_sep<7, true>(a, s); break;
+        case 8: launch_sep<8, true>(a, s); break;
+        }
+    } else {
+        switch (n) {
+        case 1: launch_sep<1, false>(a, s); break;
+        case 2: launch_sep<2, false>(a, s); break;
+        case 3: launch_sep<3, false>(a, s); break;
+        case 4: launch_sep<4, false>(a, s); break;
+        case 5: launch_sep<5, false>(a, s); break;
+        case 6: launch_sep<6, false>(a, s); break;
+        }
     }
 }
 
@@ -366,6 +409,7 @@ int check_sep(const mk_separate_cfg *cfg, int32_t npairs) {
     const mk_tune &t = cfg->tune;
     if (t.block && t.block != SEP_BLOCK) return MK_E_ARG;
     if (t.tile > 64) return MK_E_ARG;
+    if (cfg->max_depth > MK_MAX_STACK) return MK_E_ARG;
     return MK_OK;
 }
 
@@ -402,7 +446,11 @@ int64_t separate_walk(const mk_separate_cfg *cfg, SepArgs &a, const cudaStream_t
             a.f_lo = cfg->frame_lo;
             a.f_hi = cfg->frame_hi;
             a.full_range = (cfg->frame_lo == 0 && cfg->frame_hi >= kf) ? 1 : 0;
-            const uint64_t w0 = cfg->frame_lo / 32, w1 = cfg->frame_lo >= hi ? w0 : (hi + 31) / 32;
+            // the first word rounded down to a multiple of 8 (so every thread's
+            // first word is a multiple of its unit count); the frames below
+            // frame_lo are masked off as the window demands
+            const uint64_t w0 = (cfg->frame_lo / 32) & ~(uint64_t)7;
+            const uint64_t w1 = cfg->frame_lo >= hi ? w0 : (hi + 31) / 32;
             for (uint64_t w = w0; w < w1; w += chunk_words) {
                 a.word_lo = w;
                 a.word_hi = w + chunk_words < w1 ? w + chunk_words : w1;
@@ -459,6 +507,7 @@ extern "C" int mk_separate(const mk_program *d_phi, const mk_program *d_psi, int
     a.psi = d_psi;
     a.npairs = npairs;
     a.tile = cfg->tune.tile ? cfg->tune.tile : 16;
+    a.depth = cfg->max_depth ? cfg->max_depth : MK_MAX_STACK;
     a.S = cfg->samples;
     a.split = d_split;
     a.status = d_status;

@@ -147,6 +147,58 @@ def source_ops_per_eval(text, n):
     return (n * nb + n * n * nm + n) / 32.0
 
 
+# The five-world census as three mk_census calls over one program batch:
+# the dominant K n=5 layer alone (timed on its own by the bench), K at
+# n = 1..4, and T/S4/S5 at n = 1..5.
+CENSUS5_CALLS = ((("K",), 5, 5), (("K",), 1, 4), (("T", "S4", "S5"), 1, 5))
+
+
+def census_call_plan(progs, samples, d_samples_ptr, device, calls=CENSUS5_CALLS):
+    """Configurations, workspaces and output buffers of a multi-call census
+    (the caller keeps the programs and the sampled-valuation table on the
+    device).  Returns one dict per call: classes, n_min, n_max, cfg, ws,
+    ws_bytes, out ([nprog][classes][n][3] int64), launches."""
+    nprog = len(progs)
+    depth = max(1, int(progs["depth"].max())) if nprog else 1
+    plan = []
+    for classes, lo, hi in calls:
+        bits = 0
+        for c in classes:
+            bits |= mk.CLASS_BITS[c]
+        cfg = mk.census_cfg(bits, lo, hi, samples, d_samples_ptr, max_depth=depth)
+        ws = mk.census_workspace_size(cfg, nprog)
+        plan.append({"classes": classes, "n_min": lo, "n_max": hi, "cfg": cfg,
+                     "ws": torch.empty(max(ws, 1), dtype=torch.uint8, device=device), "ws_bytes": ws,
+                     "out": torch.empty(nprog * len(classes) * (hi - lo + 1) * 3, dtype=torch.int64, device=device),
+                     "launches": mk.census_launches(cfg, nprog)})
+    return plan
+
+
+def run_census_plan(plan, d_progs_ptr, nprog, d_status_ptr, stream_ptr, calls=None):
+    """Issues the plan's mk_census calls (all, or the given indices) on the stream."""
+    for i, c in enumerate(plan):
+        if calls is None or i in calls:
+            mk.census_raw(d_progs_ptr, nprog, c["cfg"], c["out"].data_ptr(), d_status_ptr, c["ws"].data_ptr(),
+                          c["ws_bytes"], stream_ptr)
+
+
+def gather_census_plan(plan, nprog, classes=CLASSES, n_min=1, n_max=5):
+    """The plan's outputs as one uint64 array [nprog][classes][n][3]
+    (layers no call computed stay zero)."""
+    out = np.zeros((nprog, len(classes), n_max - n_min + 1, 3), np.uint64)
+    for c in plan:
+        r = c["out"].cpu().numpy().view(np.uint64).reshape(nprog, len(c["classes"]), c["n_max"] - c["n_min"] + 1, 3)
+        for j, cls in enumerate(c["classes"]):
+            for n in range(c["n_min"], c["n_max"] + 1):
+                out[:, classes.index(cls), n - n_min] = r[:, j, n - c["n_min"]]
+    return out
+
+
+# The separation workload's search: every frame of 1..6 worlds, then 1e8
+# sampled relations of 7 and 8 worlds (seed 4) for pairs still unsplit.
+SEPARATION_SEARCH = dict(n_exh_min=1, n_exh_max=6, n_smp_min=7, n_smp_max=8, frames_per_n=100_000_000, seed=4)
+
+
 class SeparateJob:
     """Distinguishing-pair search for a list of (phi, psi) texts."""
 
@@ -165,9 +217,10 @@ class SeparateJob:
         self.d_pa = _dev_bytes(self.pa, self.device)
         self.d_pb = _dev_bytes(self.pb, self.device)
         self.d_samples = _dev_bytes(self.sample_table, self.device) if samples else None
+        depth = max([1] + [int(p["depth"]) for p in self.pa] + [int(p["depth"]) for p in self.pb])
         self.cfg = mk.separate_cfg(n_exh_min, n_exh_max, n_smp_min, n_smp_max, samples,
                                    self.d_samples.data_ptr() if samples else 0, frames_per_n, seed,
-                                   frame_lo, frame_hi, tune)
+                                   frame_lo, frame_hi, tune, max_depth=depth)
         self.ws_bytes = mk.separate_workspace_size(self.cfg, self.npairs)
         self.d_ws = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=self.device)
         self.d_split = torch.empty(self.npairs, dtype=torch.int64, device=self.device)
@@ -275,7 +328,11 @@ class UnevenJob:
 
 # ------------------------------------------------------------------ autotuner
 
-_TUNE_CACHE = None
+# the swept grid: valuations per dispatched instruction, CTA size, and
+# formulas per tile of each of the plan's four length buckets
+TUNE_UNITS = (4, 8)
+TUNE_BLOCKS = (128, 256)
+TUNE_TILES = (4, 8, 16, 32, 64)
 
 
 def _cache_path():
@@ -283,19 +340,27 @@ def _cache_path():
     return os.path.join(os.path.dirname(mk.LIB_PATH), "autotune.json")
 
 
-def _load_cache():
+def _load_cache(path):
     import json
     import os
-    global _TUNE_CACHE
-    if _TUNE_CACHE is None:
-        p = _cache_path()
-        _TUNE_CACHE = json.load(open(p)) if os.path.exists(p) else {}
-    return _TUNE_CACHE
+    return json.load(open(path)) if os.path.exists(path) else {}
 
 
-def _store_cache():
+def _store_cache(path, cache):
     import json
-    json.dump(_TUNE_CACHE, open(_cache_path(), "w"), indent=1, sort_keys=True)
+    import os
+    tmp = "%s.tmp%d" % (path, os.getpid())
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def tune_cache_key(gpu_name, sms, samples, n_maxes):
+    """Cache key of an uneven-batch tune: the GPU (name and SM count, which
+    set the waves a persistent grid fills) and the batch's shape (sampled
+    valuations S and the set of n_max values, which set the layers and their
+    valuation counts).  The per-bucket tile sizes are part of the tune."""
+    return "%s|%d|uneven|S=%d|n=%s" % (gpu_name, int(sms), int(samples), sorted({int(n) for n in n_maxes}))
 
 
 def _time_graph(job, reps=2):
@@ -312,7 +377,8 @@ def _time_graph(job, reps=2):
     return e0.elapsed_time(e1) / reps
 
 
-def autotune_uneven(items, samples=64, seed=3, sample_size=2400, device="cuda", use_cache=True, log=None):
+def autotune_uneven(items, samples=64, seed=3, sample_size=2400, device="cuda", use_cache=True, log=None,
+                    cache_path=None):
     """Pick the persistent launch's CTA size, valuations per dispatched
     instruction (units) and formulas per tile for each length bucket.
 
@@ -320,11 +386,12 @@ def autotune_uneven(items, samples=64, seed=3, sample_size=2400, device="cuda", 
     bucket and class represented in proportion): first (units, block) with
     16-formula tiles, then each bucket's tile size in {4, 8, 16, 32, 64} with
     the others fixed; each candidate is timed as a CUDA-graph replay.  The
-    choice is cached per (GPU name, SM count, samples, n_max set)."""
+    choice is cached (``cache_path``, default beside libmk) under
+    tune_cache_key(GPU name, SM count, samples, n_max set)."""
     props = torch.cuda.get_device_properties(torch.device(device))
-    nmaxes = sorted({n for _, _, n in items})
-    key = "%s|%d|uneven|S=%d|n=%s" % (props.name, props.multi_processor_count, samples, nmaxes)
-    cache = _load_cache()
+    key = tune_cache_key(props.name, props.multi_processor_count, samples, [n for _, _, n in items])
+    cache_path = cache_path or _cache_path()
+    cache = _load_cache(cache_path)
     if use_cache and key in cache:
         return cache[key]
     step = max(1, len(items) // sample_size)
@@ -341,14 +408,16 @@ def autotune_uneven(items, samples=64, seed=3, sample_size=2400, device="cuda", 
         return ms
 
     best = None
-    for units in (4, 8):
-        for block in (128, 256):
+    for units in TUNE_UNITS:
+        for block in TUNE_BLOCKS:
             ms = run(units, block, (16, 16, 16, 16))
             if best is None or ms < best[0]:
                 best = (ms, units, block, [16, 16, 16, 16])
     _, units, block, tiles = best
     for b in range(4):
-        for t in (4, 8, 32, 64):
+        for t in TUNE_TILES:
+            if t == tiles[b]:
+                continue
             cand = list(tiles)
             cand[b] = t
             ms = run(units, block, tuple(cand))
@@ -358,7 +427,7 @@ def autotune_uneven(items, samples=64, seed=3, sample_size=2400, device="cuda", 
     choice = {"units": best[1], "block": best[2], "tiles": best[3], "ms_sample": best[0],
               "sample_size": len(sample), "trials": trials}
     cache[key] = choice
-    _store_cache()
+    _store_cache(cache_path, cache)
     return choice
 
 

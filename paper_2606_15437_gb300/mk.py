@@ -80,7 +80,8 @@ class mk_separate_cfg(ctypes.Structure):
                 ("n_smp_min", ctypes.c_uint8), ("n_smp_max", ctypes.c_uint8),
                 ("samples", ctypes.c_uint32), ("d_samples", ctypes.c_void_p),
                 ("frames_per_n", ctypes.c_uint64), ("seed", ctypes.c_uint64),
-                ("frame_lo", ctypes.c_uint64), ("frame_hi", ctypes.c_uint64), ("tune", mk_tune)]
+                ("frame_lo", ctypes.c_uint64), ("frame_hi", ctypes.c_uint64), ("tune", mk_tune),
+                ("max_depth", ctypes.c_uint8)]
 
 
 PROGRAM_DTYPE = np.dtype([("nodes", "<u2"), ("n_instr", "u1"), ("nvars", "u1"), ("modal_depth", "u1"),
@@ -432,8 +433,9 @@ def sample_relation(seed, n, s):
 # --------------------------------------------------------- separation
 
 def separate_cfg(n_exh_min=1, n_exh_max=6, n_smp_min=0, n_smp_max=0, samples=0, d_samples=0,
-                 frames_per_n=0, seed=0, frame_lo=0, frame_hi=NO_KEY, tune=None):
+                 frames_per_n=0, seed=0, frame_lo=0, frame_hi=NO_KEY, tune=None, max_depth=0):
     cfg = mk_separate_cfg()
+    cfg.max_depth = max_depth
     cfg.n_exh_min, cfg.n_exh_max = n_exh_min, n_exh_max
     cfg.n_smp_min, cfg.n_smp_max = n_smp_min, n_smp_max
     cfg.samples = samples

@@ -99,3 +99,31 @@ def test_uneven_graph_replay_identical():
             cert = mk.witness_cert(mk.program_at(job.progs, j), t, c, nmax, job.S,
                                    job.sample_table[nmax], key)
             assert mk.certify_struct(cert) == 1
+
+
+def test_autotuner_choice_is_on_the_grid_exact_and_cached(tmp_path, monkeypatch):
+    """The autotuner returns a point of its swept grid (the fastest trial it
+    timed), the chosen tune gives bit-identical results to the default one,
+    and the choice is cached under the GPU's name and SM count and the
+    batch's shape: a second call returns it without timing anything."""
+    from paper_2606_15437_gb300 import engine as E
+    items = W.uneven_formulas(3)[:900]
+    cache = str(tmp_path / "tune.json")
+    choice = E.autotune_uneven(items, samples=64, seed=3, sample_size=300, use_cache=True, cache_path=cache)
+    assert choice["units"] in E.TUNE_UNITS and choice["block"] in E.TUNE_BLOCKS
+    assert len(choice["tiles"]) == 4 and all(t in E.TUNE_TILES for t in choice["tiles"])
+    assert choice["ms_sample"] == min(t["ms"] for t in choice["trials"])
+    tuned = E.UnevenJob(items, samples=64, seed=3, tiles=tuple(choice["tiles"]),
+                        tune={"units": choice["units"], "block": choice["block"]})
+    tuned.launch()
+    default = E.UnevenJob(items, samples=64, seed=3)
+    default.launch()
+    assert np.array_equal(tuned.results(), default.results())
+    props = torch.cuda.get_device_properties(0)
+    key = E.tune_cache_key(props.name, props.multi_processor_count, 64, [n for _, _, n in items])
+    assert E._load_cache(cache)[key]["tiles"] == choice["tiles"]
+
+    def no_timing(*a, **k):
+        raise AssertionError("a cached tune must not be timed again")
+    monkeypatch.setattr(E, "_time_graph", no_timing)
+    assert E.autotune_uneven(items, samples=64, seed=3, sample_size=300, cache_path=cache) == choice
