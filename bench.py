@@ -54,10 +54,10 @@ DRAM_BYTES_PER_PAIR_MLP = (10058240 + 24808704) / 77824
 DRAM_BYTES_PER_RELATION_STRESS = 1339392 / 65536
 # census_queue_kernel<5, 4, 128> on 2,000 uneven-batch formulas: 1.41 MB read
 DRAM_BYTES_PER_FORMULA_UNEVEN = 1411840 / 2000
-# separate_kernel<6> on one 2^27-frame chunk of 64 of the bench's late pairs
-# (ncu capture of the separation6:64 profile case), per pair staged; None
-# until captured
-DRAM_BYTES_PER_PAIR_SEPARATION6 = None
+# separate_kernel<6, 4, 256, 0> on one 2^27-frame chunk of 64 of the bench's
+# late pairs (ncu capture of the separation6:64 profile case): 93,184 B read,
+# 0 written, per pair staged
+DRAM_BYTES_PER_PAIR_SEPARATION6 = 93184 / 64
 
 
 def parse():

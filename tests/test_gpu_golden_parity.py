@@ -143,3 +143,31 @@ def test_separation_workload_first_splits_equal_the_oracle():
                 break
     print("separation splits checked against the oracle:", checked)
     assert checked["le5"] > 800 and checked["n6"] > 0
+
+
+def test_uneven_batch_larger_layers_equal_the_oracle():
+    """The uneven batch (20,000 jobs, own class and n_max each, S = 64) in one
+    persistent launch: the four- and five-world layers of a seeded subset of
+    jobs against the oracle's stored results (tests/golden/make_uneven_golden.py),
+    and a graph replay of the same call gives the same results."""
+    from paper_2606_15437_gb300 import engine as E
+    name = "uneven_subset.tsv"
+    _need(name)
+    items = W.uneven_formulas(3)
+    sha = hashlib.sha256("\n".join("%s\t%s\t%d" % it for it in items).encode()).hexdigest()
+    assert G.header_values(name)["items_sha256"] == sha
+    job = E.UnevenJob(items, samples=64, seed=3)
+    job.launch()
+    res = job.results().copy()
+    want = G.census_rows(name)
+    assert len(want) == 440
+    for (j, c, n), (cm, fr, w) in want.items():
+        assert items[j][1] == c and items[j][2] >= n
+        got = tuple(int(x) for x in res[j, n - 1])
+        assert got == (cm, fr, _key(w)), (j, items[j], n)
+        if w is not None:
+            cert = mk.witness_cert(mk.program_at(job.progs, j), items[j][0], c, n, 64, job.sample_table[n], got[2])
+            assert mk.certify_struct(cert) == 1
+    job.capture()
+    job.replay()
+    assert np.array_equal(job.results(), res)
