@@ -24,7 +24,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _lock = threading.Lock()
 _lib = None
 
-CLASSES = ("K", "T", "S4", "S5")
+CLASSES = ("K", "T", "S4", "S5", "K4")
 
 
 def build(force=False):

@@ -16,7 +16,7 @@
  *   satisfaction  w |= []phi iff for all v, R(w,v) implies v |= phi;
  *                 w |= <>phi iff some v has R(w,v) and v |= phi   (Sec. 2)
  *   classes       K all frames, T reflexive, S4 reflexive+transitive,
- *                 S5 reflexive+transitive+symmetric             (Sec. 2)
+ *                 S5 reflexive+transitive+symmetric, K4 transitive (Sec. 2)
  *   countermodel  (F, V, w) with M,w not|= phi                  (Sec. 2)
  *   census        per (formula, class, n): the number of refuted
  *                 (frame, valuation) pairs, the number of refuted frames,
@@ -211,9 +211,11 @@ static int symmetric(int n, const uint8_t *R) {
         if (R[w * n + v] && !R[v * n + w]) return 0;
     return 1;
 }
-/* cls: 0 = K, 1 = T, 2 = S4, 3 = S5 */
+/* cls: 0 = K, 1 = T, 2 = S4, 3 = S5, 4 = K4 (transitive frames, the frames
+   of the logic K4: Sec. 2 names K4 beside T, S4 and S5) */
 static int in_class(int cls, int n, const uint8_t *R) {
     if (cls == 0) return 1;
+    if (cls == 4) return transitive(n, R);
     if (!reflexive(n, R)) return 0;
     if (cls == 1) return 1;
     if (!transitive(n, R)) return 0;
@@ -301,7 +303,7 @@ int orc_census(const char *text, int cls, int n, uint32_t S, const uint32_t *sam
                uint64_t f_lo, uint64_t f_hi, orc_census_out *out) {
     oform f;
     memset(out, 0, sizeof(*out));
-    if (n < 1 || n > 6 || cls < 0 || cls > 3) return -2;
+    if (n < 1 || n > 6 || cls < 0 || cls > 4) return -2;
     if (parse(text, &f)) return -1;
     int k = f.nvars;
     int exh = exhaustive_vals(k, n, S);

@@ -132,7 +132,7 @@ def in_class(cls, n, R):
     refl = all((w, w) in R for w in range(n))
     trans = all((w, u) in R for (w, v) in R for (x, u) in R if v == x)
     sym = all((v, w) in R for (w, v) in R)
-    return {"K": True, "T": refl, "S4": refl and trans, "S5": refl and trans and sym}[cls]
+    return {"K": True, "T": refl, "S4": refl and trans, "S5": refl and trans and sym, "K4": trans}[cls]
 
 
 def all_valuations(k, n):

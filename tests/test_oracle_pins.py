@@ -447,3 +447,37 @@ def test_matched_rows_have_the_table_shapes():
     t = [r for r in W.matched_rows() if r["cls"] == "T"][0]
     got = oracle.census(t["text"], "T", 5, f_lo=t["lo"], f_hi=t["hi"])
     assert got["frames"] == t["frames"] == 2049
+
+
+# ------------------------------------------------------------------ K4 frames
+
+def test_k4_class_is_the_transitive_frames():
+    # K4's frames are the transitive relations (Sec. 2 names K4 beside T, S4,
+    # S5): their number on n labelled points is OEIS A006905
+    assert [oracle.class_size("K4", n) for n in range(1, 5)] == [2, 13, 171, 3994]
+    assert [pyref.frames_in_class("K4", n) for n in range(1, 4)] == [2, 13, 171]
+
+
+def test_k4_correspondences():
+    # 4 = []p -> [][]p is valid exactly on transitive frames, so on every K4
+    # frame; T = []p -> p is valid exactly on reflexive frames, so on K4 it is
+    # refuted on the transitive frames that are not reflexive (K4 minus S4)
+    for n in range(1, 5):
+        assert oracle.census("[]p -> [][]p", "K4", n)["cm_count"] == 0
+        r = oracle.census("[]p -> p", "K4", n)
+        assert r["frames_refuted"] == oracle.class_size("K4", n) - oracle.class_size("S4", n)
+    # and the K4 census agrees with the set-based path by brute force
+    for t in ("[]p -> p", "<>[]p -> []<>p", "[](p -> q) | <>~q", "<>T -> []<>T"):
+        for n in (1, 2, 3):
+            a = oracle.census(t, "K4", n)
+            assert (a["cm_count"], a["frames_refuted"], a["witness"]) == pyref.census(t, "K4", n), (t, n)
+
+
+def test_k4_window_of_table4():
+    # Table 4's K4 row filters 304 frames: read as the first 304 transitive
+    # five-world frames in K order, which end below K index 653
+    r = [x for x in W.matched_rows() if x["cls"] == "K4"][0]
+    assert r["frames"] == 304 and (r["lo"], r["hi"]) == (0, 653)
+    got = oracle.census(r["text"], "K4", 5, f_lo=0, f_hi=653)
+    assert got["frames"] == 304
+    assert oracle.census(r["text"], "K4", 5, f_lo=0, f_hi=652)["frames"] == 303
