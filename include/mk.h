@@ -78,6 +78,8 @@ extern "C" {
 #define MK_CLASS_T 2u        /* reflexive                                     */
 #define MK_CLASS_S4 4u       /* reflexive and transitive (preorders)          */
 #define MK_CLASS_S5 8u       /* equivalence relations                         */
+#define MK_CLASS_K4 16u      /* transitive (the frames of K4; not in the      */
+                             /* uneven path, whose jobs are K, T, S4 or S5)    */
 
 /* --------------------------------------------------- compiled programs */
 /* A program is postfix code for an accumulator machine over truth sets (the
@@ -176,7 +178,7 @@ typedef struct {
 } mk_result;
 
 /* Workspace bytes mk_census needs for this configuration and batch: the
-   S4/S5 frame lists and, when some layer splits its valuations, a bitmap of
+   S4/S5/K4 frame lists and, when some layer splits its valuations, a bitmap of
    nprog x (that layer's frame words) u32 words in which the chunks OR their
    refuted frames, plus one u32 counter per formula tile (the last CTA of a
    tile to finish counts the bitmap).  Given less (but at least the lists'
@@ -184,7 +186,7 @@ typedef struct {
 size_t mk_census_workspace_size(const mk_census_cfg *cfg, int32_t nprog);
 
 /* Census (Alg. 1 over every selected (class, n) layer, Thm. 2): for each
-   program p, each selected class c (in the order K, T, S4, S5) and each
+   program p, each selected class c (in the order K, T, S4, S5, K4) and each
    n in [n_min, n_max], writes
        d_out[(p * ncls + c) * (n_max - n_min + 1) + (n - n_min)]
    where ncls = number of selected classes.  d_progs: device [nprog]
@@ -201,8 +203,8 @@ int mk_census(const mk_program *d_progs, int32_t nprog, const mk_census_cfg *cfg
    is a packaging of mk_census.  Arguments and results are those of
    mk_census; the scratch space is a fixed array of MK_NOALLOC_SCRATCH_BYTES
    inside the library, held on every GPU that loads it until the process
-   exits.  Configurations whose S4/S5 frame lists exceed that limit (S4 or
-   S5 at n = 6) are rejected with MK_E_WORKSPACE before anything is
+   exits.  Configurations whose S4/S5/K4 frame lists exceed that limit (S4 or
+   S5 at n = 6, K4 at n >= 5) are rejected with MK_E_WORKSPACE before anything is
    launched; layers split their valuations only when the split bitmap also
    fits (mk_census_workspace_size <= the limit).  Every call made outside
    stream capture looks up the array's address on the current device
@@ -284,7 +286,8 @@ int mk_census_uneven(const mk_program *d_progs, const mk_job *d_jobs, int32_t nj
                      void *stream);
 
 /* Number of class-c frames on n worlds that mk_census enumerates (K: 2^(n^2),
-   T: 2^(n^2-n), S4: preorders, S5: equivalence relations); 0 if n > 6. */
+   T: 2^(n^2-n), S4: preorders, S5: equivalence relations, K4: transitive
+   relations); 0 if n > 6. */
 uint64_t mk_class_frames(uint32_t cls, int32_t n);
 
 /* ------------------------------------------------------- certificates */
@@ -293,7 +296,8 @@ typedef struct {
     const char *psi;           /* NULL: countermodel certificate for phi;        */
                                /* else: a world where phi and psi disagree       */
     uint8_t n;                 /* worlds, 1..32                                  */
-    uint8_t cls;               /* 0 K, 1 T, 2 S4, 3 S5: the frame must be in it  */
+    uint8_t cls;               /* 0 K, 1 T, 2 S4, 3 S5, 4 K4: the frame must be  */
+                               /* in it                                          */
     uint8_t world;             /* the pointed world                              */
     uint8_t reserved;
     uint32_t succ[MK_MAX_CERT_WORLDS];  /* successor masks                       */

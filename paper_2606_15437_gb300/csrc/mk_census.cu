@@ -25,7 +25,9 @@
 // Classes: K frames are every index; T frames are enumerated by their
 // compact index (diagonal forced on); S4 and S5 frames are first listed by a
 // three-kernel filter over the T frames (count, scan, write; ascending K
-// order) into the caller's workspace, then scanned from that list.
+// order) into the caller's workspace, then scanned from that list; K4
+// frames (transitive, not necessarily reflexive) are listed the same way by
+// a filter over the K frames.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -518,28 +520,33 @@ __global__ void __launch_bounds__(BLOCK) census_queue_kernel(QueueArgs a) {
 
 __global__ void reset_cursor_kernel(uint32_t *cursor) { *cursor = 0; }
 
-// ---------------------------------------------------- S4 / S5 frame lists
+// ----------------------------------------------- S4 / S5 / K4 frame lists
+
+// List kinds: S4 and S5 filter the T frames (word = 32 compact indices) by
+// transitivity (S5: and symmetry); K4 filters the K frames by transitivity.
+constexpr int LIST_S4 = 0, LIST_S5 = 1, LIST_K4 = 2, NLISTS = 3;
 
 template <int N>
-__device__ __forceinline__ uint32_t class_word_mask(uint64_t word, uint64_t tframes, bool sym) {
+__device__ __forceinline__ uint32_t class_word_mask(uint64_t word, uint64_t nframes, int kind) {
     uint32_t E[N * N];
-    t_frame_word<N>(word, E);
+    if (kind == LIST_K4) k_frame_word<N>(word, E);
+    else t_frame_word<N>(word, E);
     const uint64_t base = word << 5;
     uint32_t valid = 0;
-    if (base < tframes) {
-        const uint64_t left = tframes - base;
+    if (base < nframes) {
+        const uint64_t left = nframes - base;
         valid = left >= 32 ? 0xFFFFFFFFu : ((1u << left) - 1u);
     }
-    return valid & preorder_mask<N>(E, sym);
+    return valid & preorder_mask<N>(E, kind == LIST_S5);
 }
 
 template <int N>
-__global__ void __launch_bounds__(256) list_count_kernel(uint32_t *blk, uint64_t nwords, uint64_t tframes, int sym) {
+__global__ void __launch_bounds__(256) list_count_kernel(uint32_t *blk, uint64_t nwords, uint64_t nframes, int kind) {
     __shared__ uint32_t s_sum;
     if (threadIdx.x == 0) s_sum = 0;
     __syncthreads();
     const uint64_t word = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t m = word < nwords ? class_word_mask<N>(word, tframes, sym != 0) : 0u;
+    const uint32_t m = word < nwords ? class_word_mask<N>(word, nframes, kind) : 0u;
     const uint32_t s = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(m));
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(&s_sum, s);
     __syncthreads();
@@ -573,11 +580,11 @@ __global__ void __launch_bounds__(1024) list_scan_kernel(uint32_t *blk, uint32_t
 
 template <int N>
 __global__ void __launch_bounds__(256) list_write_kernel(const uint32_t *blk, uint64_t *list, uint64_t cap,
-                                                         uint64_t nwords, uint64_t tframes, int sym,
+                                                         uint64_t nwords, uint64_t nframes, int kind,
                                                          int32_t *status) {
     __shared__ uint32_t s_warp[8];
     const uint64_t word = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t m = word < nwords ? class_word_mask<N>(word, tframes, sym != 0) : 0u;
+    const uint32_t m = word < nwords ? class_word_mask<N>(word, nframes, kind) : 0u;
     const uint32_t c = (uint32_t)__popc(m);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // inclusive warp prefix of c
@@ -594,7 +601,8 @@ __global__ void __launch_bounds__(256) list_write_kernel(const uint32_t *blk, ui
     uint64_t pos = (uint64_t)blk[blockIdx.x] + before + (x - c);
     for (int l = 0; l < 32; ++l) {
         if ((m >> l) & 1u) {
-            if (pos < cap) list[pos] = t_to_k((word << 5) + (uint64_t)l, N);
+            const uint64_t ord = (word << 5) + (uint64_t)l;
+            if (pos < cap) list[pos] = kind == LIST_K4 ? ord : t_to_k(ord, N);
             else atomicOr(status, (int)MK_ST_INTERNAL);
             ++pos;
         }
@@ -611,8 +619,18 @@ using namespace mkd;
 
 const uint64_t kPreorders[7] = {0, 1, 4, 29, 355, 6942, 209527};
 const uint64_t kEquivalences[7] = {0, 1, 2, 5, 15, 52, 203};
+const uint64_t kTransitive[7] = {0, 2, 13, 171, 3994, 154303, 9415189};   // OEIS A006905
+constexpr uint32_t kAllClasses = MK_CLASS_K | MK_CLASS_T | MK_CLASS_S4 | MK_CLASS_S5 | MK_CLASS_K4;
+constexpr int kNumClasses = 5;   // class index c <-> bit 1 << c: K, T, S4, S5, K4
 
-int class_count(uint32_t classes) { return __builtin_popcount(classes & 15u); }
+int class_count(uint32_t classes) { return __builtin_popcount(classes & kAllClasses); }
+
+// list kind of class index c >= 2
+int list_kind(int c) { return c == 2 ? LIST_S4 : c == 3 ? LIST_S5 : LIST_K4; }
+uint32_t list_class_bit(int kind) { return kind == LIST_S4 ? MK_CLASS_S4 : kind == LIST_S5 ? MK_CLASS_S5 : MK_CLASS_K4; }
+uint64_t list_cap(int kind, int n) {
+    return kind == LIST_S4 ? kPreorders[n] : kind == LIST_S5 ? kEquivalences[n] : kTransitive[n];
+}
 
 uint64_t t_frames(int n) { return 1ull << (n * n - n); }
 
@@ -621,7 +639,8 @@ uint64_t layer_frames(int cls, int n) {
     case 0: return 1ull << (n * n);
     case 1: return t_frames(n);
     case 2: return kPreorders[n];
-    default: return kEquivalences[n];
+    case 3: return kEquivalences[n];
+    default: return kTransitive[n];
     }
 }
 
@@ -694,8 +713,8 @@ uint32_t layer_vsplit(const mk_census_cfg *cfg, int n, uint64_t words, int32_t n
 }
 
 struct ListPlan {
-    size_t list_off[2][7];   // [S4, S5][n]: byte offset of the list
-    size_t len_off[2][7];    // device count
+    size_t list_off[NLISTS][7];   // [S4, S5, K4][n]: byte offset of the list
+    size_t len_off[NLISTS][7];    // device count
     size_t blk_off;          // scan scratch
     size_t cursor_off;       // queue cursor
     size_t total;
@@ -709,16 +728,16 @@ ListPlan plan_lists(uint32_t classes, int n_min, int n_max) {
     std::memset(&p, 0, sizeof(p));
     size_t off = 0;
     uint64_t max_blk = 1;
-    for (int c = 0; c < 2; ++c) {
-        const uint32_t bit = c == 0 ? MK_CLASS_S4 : MK_CLASS_S5;
-        if (!(classes & bit)) continue;
+    for (int c = 0; c < NLISTS; ++c) {
+        if (!(classes & list_class_bit(c))) continue;
         for (int n = n_min; n <= n_max; ++n) {
-            const uint64_t cap = c == 0 ? kPreorders[n] : kEquivalences[n];
+            const uint64_t cap = list_cap(c, n);
             p.len_off[c][n] = off;
             off = align256(off + 8);
             p.list_off[c][n] = off;
             off = align256(off + cap * 8);
-            const uint64_t nw = (t_frames(n) + 31) / 32;
+            const uint64_t scanned = c == LIST_K4 ? (1ull << (n * n)) : t_frames(n);
+            const uint64_t nw = (scanned + 31) / 32;
             const uint64_t nb = (nw + 255) / 256;
             if (nb > max_blk) max_blk = nb;
         }
@@ -745,7 +764,7 @@ CensusPlan plan_census(const mk_census_cfg *cfg, int32_t nprog) {
     p.lists = plan_lists(cfg->classes, cfg->n_min, cfg->n_max);
     p.rf_off = align256(p.lists.total);
     p.rf_bytes = 0;
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < kNumClasses; ++c) {
         if (!(cfg->classes & (1u << c))) continue;
         for (int n = cfg->n_min; n <= cfg->n_max; ++n) {
             uint64_t w0, w1;
@@ -770,7 +789,7 @@ CensusPlan plan_census(const mk_census_cfg *cfg, int32_t nprog) {
 
 int check_cfg(const mk_census_cfg *cfg, int32_t nprog) {
     if (!cfg || nprog < 0) return MK_E_ARG;
-    if ((cfg->classes & 15u) == 0 || (cfg->classes & ~15u)) return MK_E_ARG;
+    if ((cfg->classes & kAllClasses) == 0 || (cfg->classes & ~kAllClasses)) return MK_E_ARG;
     if (cfg->n_min < 1 || cfg->n_max > MK_MAX_WORLDS_EXH || cfg->n_min > cfg->n_max) return MK_E_ARG;
     if ((cfg->samples == 0) != (cfg->d_samples == nullptr)) return MK_E_ARG;
     if (cfg->frame_lo > cfg->frame_hi) return MK_E_ARG;
@@ -831,18 +850,19 @@ void launch_layer_n(int n, const LayerArgs &a, int block, int units, cudaStream_
     }
 }
 
+// List of kind c at N worlds: S4/S5 filter the T frames, K4 the K frames.
 template <int N>
 void launch_list(uint8_t *ws, const ListPlan &p, int c, int32_t *status, cudaStream_t s) {
-    const uint64_t tf = t_frames(N);
-    const uint64_t nw = (tf + 31) / 32;
+    const uint64_t nf = c == LIST_K4 ? (1ull << (N * N)) : t_frames(N);
+    const uint64_t nw = (nf + 31) / 32;
     const unsigned nb = (unsigned)((nw + 255) / 256);
     uint32_t *blk = (uint32_t *)(ws + p.blk_off);
     uint64_t *len = (uint64_t *)(ws + p.len_off[c][N]);
     uint64_t *list = (uint64_t *)(ws + p.list_off[c][N]);
-    const uint64_t cap = c == 0 ? kPreorders[N] : kEquivalences[N];
-    list_count_kernel<N><<<nb, 256, 0, s>>>(blk, nw, tf, c);
+    const uint64_t cap = list_cap(c, N);
+    list_count_kernel<N><<<nb, 256, 0, s>>>(blk, nw, nf, c);
     list_scan_kernel<<<1, 1024, 0, s>>>(blk, nb, len);
-    list_write_kernel<N><<<nb, 256, 0, s>>>(blk, list, cap, nw, tf, c, status);
+    list_write_kernel<N><<<nb, 256, 0, s>>>(blk, list, cap, nw, nf, c, status);
 }
 
 void launch_list_n(int n, uint8_t *ws, const ListPlan &p, int c, int32_t *status, cudaStream_t s) {
@@ -872,6 +892,7 @@ extern "C" uint64_t mk_class_frames(uint32_t cls, int32_t n) {
     case MK_CLASS_T: return t_frames(n);
     case MK_CLASS_S4: return kPreorders[n];
     case MK_CLASS_S5: return kEquivalences[n];
+    case MK_CLASS_K4: return kTransitive[n];
     default: return 0;
     }
 }
@@ -879,10 +900,11 @@ extern "C" uint64_t mk_class_frames(uint32_t cls, int32_t n) {
 extern "C" int32_t mk_census_launches(const mk_census_cfg *cfg, int32_t nprog) {
     if (check_cfg(cfg, nprog) != MK_OK) return -1;
     const int nn = cfg->n_max - cfg->n_min + 1;
-    const int lists = ((cfg->classes & MK_CLASS_S4) ? 1 : 0) + ((cfg->classes & MK_CLASS_S5) ? 1 : 0);
+    int lists = 0;
+    for (int c = 0; c < NLISTS; ++c) lists += (cfg->classes & list_class_bit(c)) ? 1 : 0;
     if (nprog == 0) return lists * nn * 3;
     int layers = 0;
-    for (int c = 0; c < 4; ++c)
+    for (int c = 0; c < kNumClasses; ++c)
         if (cfg->classes & (1u << c))
             for (int n = cfg->n_min; n <= cfg->n_max; ++n) {
                 uint64_t w0, w1;
@@ -929,15 +951,14 @@ extern "C" int mk_census(const mk_program *d_progs, int32_t nprog, const mk_cens
     const int depth = cfg->max_depth ? cfg->max_depth : MK_MAX_STACK;
     const int units = cfg->tune.units ? cfg->tune.units : 8;
 
-    // class lists for S4 / S5
-    for (int c = 0; c < 2; ++c) {
-        const uint32_t bit = c == 0 ? MK_CLASS_S4 : MK_CLASS_S5;
-        if (!(cfg->classes & bit)) continue;
+    // class lists for S4 / S5 / K4
+    for (int c = 0; c < NLISTS; ++c) {
+        if (!(cfg->classes & list_class_bit(c))) continue;
         for (int n = cfg->n_min; n <= cfg->n_max; ++n) launch_list_n(n, ws, plan, c, d_status, s);
     }
 
     int ci = 0;
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < kNumClasses; ++c) {
         const uint32_t bit = 1u << c;
         if (!(cfg->classes & bit)) continue;
         for (int n = cfg->n_min; n <= cfg->n_max; ++n) {
@@ -966,11 +987,11 @@ extern "C" int mk_census(const mk_program *d_progs, int32_t nprog, const mk_cens
                 t.src = SRC_T;
                 t.nframes = t_frames(n);
             } else {
-                const int li = c - 2;
+                const int li = list_kind(c);
                 t.src = SRC_LIST;
                 t.flist = (const uint64_t *)(ws + plan.list_off[li][n]);
                 a.list_len = (const uint64_t *)(ws + plan.len_off[li][n]);
-                t.nframes = li == 0 ? kPreorders[n] : kEquivalences[n];
+                t.nframes = list_cap(li, n);
             }
             if (t.w1 == t.w0) continue;
             a.sp.vsplit = may_split ? layer_vsplit(cfg, n, t.w1 - t.w0, nprog) : 1;

@@ -217,6 +217,13 @@ std::vector<bool> holds(const Model &m, const Formula &f) {
 
 bool frame_in_class(const Model &m, int cls) {
     if (cls == 0) return true;
+    if (cls == 4) {                                                             // K4: transitive
+        for (int w = 0; w < m.n; w++)
+            for (int v : m.successors[w])
+                for (int u : m.successors[v])
+                    if (!related(m, w, u)) return false;
+        return true;
+    }
     for (int w = 0; w < m.n; w++) if (!related(m, w, w)) return false;          // reflexive
     if (cls == 1) return true;
     for (int w = 0; w < m.n; w++)                                               // transitive
@@ -235,7 +242,7 @@ bool frame_in_class(const Model &m, int cls) {
 extern "C" int mk_certify(const mk_cert *c) {
     if (!c || !c->phi) return MK_E_ARG;
     int n = c->n;
-    if (n < 1 || n > MK_MAX_CERT_WORLDS || c->cls > 3 || c->world >= n) return MK_E_ARG;
+    if (n < 1 || n > MK_MAX_CERT_WORLDS || c->cls > 4 || c->world >= n) return MK_E_ARG;
     uint64_t full = (n == 32) ? 0xFFFFFFFFull : ((1ull << n) - 1);
     Reader ra(tokenize(c->phi));
     FormulaPtr phi = ra.formula();

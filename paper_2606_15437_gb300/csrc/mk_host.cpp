@@ -45,6 +45,7 @@ extern "C" int mk_witness_cert(const mk_program *h_prog, const char *phi, uint32
     case MK_CLASS_T: ci = 1; break;
     case MK_CLASS_S4: ci = 2; break;
     case MK_CLASS_S5: ci = 3; break;
+    case MK_CLASS_K4: ci = 4; break;
     default: return MK_E_ARG;
     }
     const uint64_t f = key >> 27;

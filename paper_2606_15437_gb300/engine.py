@@ -11,7 +11,7 @@ import torch
 
 from . import mk, workloads
 
-CLASSES = ("K", "T", "S4", "S5")
+CLASSES = ("K", "T", "S4", "S5", "K4")
 
 
 def _stream_ptr(stream):

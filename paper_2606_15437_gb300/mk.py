@@ -18,7 +18,7 @@ MK_MAX_CODE = 96
 MK_MAX_STACK = 4
 MK_MAX_VARS = 4
 MK_MAX_CERT_WORLDS = 32
-CLASS_BITS = {"K": 1, "T": 2, "S4": 4, "S5": 8}
+CLASS_BITS = {"K": 1, "T": 2, "S4": 4, "S5": 8, "K4": 16}
 CLASS_NAMES = ("K", "T", "S4", "S5")
 NO_KEY = (1 << 64) - 1
 

@@ -270,3 +270,43 @@ def test_resumable_census_on_the_gpu(tmp_path):
     got = E.merge_census_journal(texts, CLS, 1, 4, d, **kw)
     want = E.CensusJob(texts, CLS, 1, 4, samples=256, seed=2).run()
     assert np.array_equal(got, want)
+
+
+def test_k4_class_against_the_oracle():
+    """K4 frames (transitive relations, listed on the device by filtering
+    the K frames): every count and witness against the oracle through four
+    worlds, with sampled valuations, and every witness certified in class
+    K4."""
+    texts = (["<>T -> []<>T", "[](p0 -> p1) & <>p2 -> <>(p1 & p2)"] + list(W.AXIOMS) +
+             W.pr1_formulas()[:30])
+    job = engine().CensusJob(texts, ("K4",), 1, 4, samples=16, seed=4)
+    res = job.run()
+    check_against_oracle(job, res, texts, (1, 2, 3), classes=("K4",))
+    # four worlds (3,994 transitive frames) for the first formulas: results are
+    # compared by position, so a prefix of the batch
+    check_against_oracle(job, res, texts[:9], (4,), classes=("K4",))
+
+
+def test_k4_closed_forms_through_five_worlds():
+    # class sizes (OEIS A006905), 4 valid on every transitive frame, T
+    # refuted exactly on the transitive frames that are not reflexive
+    texts = ["F", W.FOUR_AXIOM, W.T_AXIOM]
+    job = engine().CensusJob(texts, ("K4", "S4"), 1, 5, samples=0)
+    res = job.run()
+    sizes = [2, 13, 171, 3994, 154303]
+    for n in range(1, 6):
+        assert int(res[0, 1, n - 1, 1]) == sizes[n - 1]
+        assert int(res[1, 1, n - 1, 0]) == 0 and int(res[1, 1, n - 1, 2]) == mk.NO_KEY
+        assert int(res[2, 1, n - 1, 1]) == sizes[n - 1] - int(res[0, 0, n - 1, 1])
+
+
+def test_k4_window_of_table4_matched_row():
+    # Table 4's K4 row: the first 304 transitive five-world frames (K index < 653)
+    r = [x for x in W.matched_rows() if x["cls"] == "K4"][0]
+    job = engine().CensusJob(["F", r["text"], "[]p -> p"], ("K4",), 5, 5, samples=0, frame_lo=r["lo"],
+                             frame_hi=r["hi"])
+    res = job.run()
+    assert int(res[0, 0, 0, 1]) == r["frames"] == 304
+    for i, t in enumerate(["F", r["text"], "[]p -> p"]):
+        want = oracle.census(t, "K4", 5, f_lo=r["lo"], f_hi=r["hi"])
+        assert tuple(int(x) for x in res[i, 0, 0]) == (want["cm_count"], want["frames_refuted"], oracle_key(want))
