@@ -1,0 +1,184 @@
+"""Writes the oracle's census results for the five-world census batch.
+
+The batch is the seeded synthetic corpus that stands in for the paper's
+5,624-formula census of Sec. 6 (5,621 random formulas of length 3-24, modal
+depth 1-4 and 0-3 variables, plus the K, T and 4 axioms), over classes
+K/T/S4/S5 with S = 256 sampled valuations per layer (seed 2).  Every value
+written here comes from ``oracle.census`` (the recursive satisfaction of
+Sec. 2 over explicit relations, the corpus scan of Alg. 1 in Sec. 4); the
+inputs come from the seeded generators of ``workloads``.  Nothing of the CUDA
+path is imported.
+
+Two files:
+
+* ``census5_n1to4.tsv.gz`` -- every formula, every class, n = 1..4;
+* ``census5_n5_subset.tsv`` -- full five-world layers (all 2^25 K frames,
+  2^20 T frames, the 6,942 S4 and 52 S5 frames) for a stratified subset:
+  per variable count k = 0..3 the longest formula and the deepest of the
+  longest, seeded random picks (40 / 20 / 2 / 2 for k = 0 / 1 / 2 / 3), and
+  the three axioms.
+
+Rows: formula index, class, n, cm_count, frames_refuted, witness as
+"frame,valuation,world" (K index; valuation index or sample slot; least
+world) or "-".  The header carries the SHA-256 of the formula texts so a test
+can tell that its inputs are the ones these values were computed for.
+
+Run from the repository root (hours of CPU for the n = 5 part; the script
+resumes from its partial file):
+
+    python tests/golden/make_census5_golden.py --part n1to4
+    python tests/golden/make_census5_golden.py --part n5
+"""
+import argparse
+import gzip
+import hashlib
+import os
+import random
+import re
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle                                          # noqa: E402
+from paper_2606_15437_gb300 import workloads as W      # noqa: E402  (inputs only)
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SEED, S = 2, 256
+CLASSES = ("K", "T", "S4", "S5")
+SUBSET_RANDOM = {0: 40, 1: 20, 2: 2, 3: 2}
+
+
+def texts_sha(texts):
+    return hashlib.sha256("\n".join(texts).encode()).hexdigest()
+
+
+def modal_depth(text):
+    """Largest nesting of [] / <> in a generated text (fully parenthesised,
+    unary operators prefixed)."""
+    toks = re.findall(r"\[\]|<>|~|\(|\)|&|\||->|p\d+|[pqrs]|T|F", text)
+    pos = 0
+
+    def unary():
+        nonlocal pos
+        t = toks[pos]
+        if t in ("[]", "<>"):
+            pos += 1
+            return 1 + unary()
+        if t == "~":
+            pos += 1
+            return unary()
+        if t == "(":
+            pos += 1
+            d = binary()
+            pos += 1                      # ")"
+            return d
+        pos += 1                          # atom or constant
+        return 0
+
+    def binary():
+        nonlocal pos
+        d = unary()
+        while pos < len(toks) and toks[pos] in ("&", "|", "->"):
+            pos += 1
+            d = max(d, unary())
+        return d
+
+    return binary()
+
+
+def n5_subset(texts):
+    """Indices of the stratified five-world subset (sorted)."""
+    ncore = len(texts) - len(W.AXIOMS)
+    info = [(oracle.nvars(t), W.nodes(t), modal_depth(t)) for t in texts[:ncore]]
+    rng = random.Random(5)
+    pick = set()
+    for k in range(4):
+        idx = [i for i in range(ncore) if info[i][0] == k]
+        pick.add(max(idx, key=lambda i: (info[i][1], -i)))                  # longest
+        pick.add(max(idx, key=lambda i: (info[i][2], info[i][1], -i)))      # deepest, then longest
+        rest = [i for i in idx if i not in pick]
+        pick.update(rng.sample(rest, SUBSET_RANDOM[k]))
+    pick.update(range(ncore, len(texts)))
+    return sorted(pick)
+
+
+def fmt(p, c, n, r):
+    w = "-" if r["witness"] is None else "%d,%d,%d" % r["witness"]
+    return "%d\t%s\t%d\t%d\t%d\t%s" % (p, c, n, r["cm_count"], r["frames_refuted"], w)
+
+
+def header(texts, what):
+    return ["# Oracle census of the five-world census batch (Sec. 4 Alg. 1; Sec. 6 corpus",
+            "# stand-in): %s." % what,
+            "# Written by tests/golden/make_census5_golden.py from oracle.census only.",
+            "# inputs: workloads.census5_formulas(seed=%d) (%d formulas), S = %d sampled valuations"
+            % (SEED, len(texts), S),
+            "# per layer from workloads.sampled_valuations(%d, n, %d)" % (SEED, S),
+            "# texts_sha256\t%s" % texts_sha(texts),
+            "# columns: formula\tclass\tn\tcm_count\tframes_refuted\twitness(frame,valuation,world)"]
+
+
+def run(texts, units, partial, log_every=200):
+    """Computes every (formula, class, n) unit not yet in ``partial``;
+    returns all rows keyed by unit."""
+    done = {}
+    if os.path.exists(partial):
+        with open(partial) as f:
+            for line in f:
+                p, c, n = line.split("\t")[:3]
+                done[(int(p), c, int(n))] = line.rstrip("\n")
+    samples = {n: W.sampled_valuations(SEED, n, S) for n in range(1, 6)}
+    t0 = time.time()
+    todo = [u for u in units if u not in done]
+    with open(partial, "a") as f:
+        for i, (p, c, n) in enumerate(todo):
+            r = oracle.census(texts[p], c, n, samples=samples[n])
+            line = fmt(p, c, n, r)
+            f.write(line + "\n")
+            f.flush()
+            done[(p, c, n)] = line
+            if i % log_every == 0:
+                print("%d/%d units, %.0f s" % (i, len(todo), time.time() - t0), flush=True)
+    return done
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--part", choices=("n1to4", "n5"), required=True)
+    ap.add_argument("--workdir", default=HERE, help="where the resumable partial file lives")
+    args = ap.parse_args()
+    texts = W.census5_formulas(SEED)
+    oracle.build()
+    if args.part == "n1to4":
+        units = [(p, c, n) for p in range(len(texts)) for c in CLASSES for n in range(1, 5)]
+        partial = os.path.join(args.workdir, "census5_n1to4.partial")
+        rows = run(texts, units, partial, log_every=2000)
+        out = os.path.join(HERE, "census5_n1to4.tsv.gz")
+        with gzip.open(out, "wt") as f:
+            f.write("\n".join(header(texts, "every formula, classes K/T/S4/S5, n = 1..4")) + "\n")
+            for u in units:
+                f.write(rows[u] + "\n")
+    else:
+        subset = n5_subset(texts)
+        # cheapest first, so a partial run covers the most formulas
+        units = [(p, c, 5) for p in subset for c in ("S5", "S4", "T", "K")]
+        units.sort(key=lambda u: (u[1] == "K", oracle.nvars(texts[u[0]]), W.nodes(texts[u[0]])))
+        partial = os.path.join(args.workdir, "census5_n5_subset.partial")
+        rows = run(texts, units, partial, log_every=1)
+        out = os.path.join(HERE, "census5_n5_subset.tsv")
+        with open(out, "w") as f:
+            f.write("\n".join(header(texts, "full n = 5 layers of a stratified subset of %d formulas "
+                                     "(per k = 0..3: longest, deepest, seeded picks 40/20/2/2; "
+                                     "the three axioms)" % len(subset))) + "\n")
+            for p in subset:
+                for c in CLASSES:
+                    f.write(rows[(p, c, 5)] + "\n")
+    if os.path.exists(partial):
+        os.remove(partial)
+    print("wrote", out)
+
+
+if __name__ == "__main__":
+    main()
