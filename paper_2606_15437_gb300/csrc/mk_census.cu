@@ -541,12 +541,13 @@ __device__ __forceinline__ uint32_t class_word_mask(uint64_t word, uint64_t nfra
 }
 
 template <int N>
-__global__ void __launch_bounds__(256) list_count_kernel(uint32_t *blk, uint64_t nwords, uint64_t nframes, int kind) {
+__global__ void __launch_bounds__(256) list_count_kernel(uint32_t *blk, uint64_t word0, uint64_t nwords,
+                                                         uint64_t nframes, int kind) {
     __shared__ uint32_t s_sum;
     if (threadIdx.x == 0) s_sum = 0;
     __syncthreads();
-    const uint64_t word = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t m = word < nwords ? class_word_mask<N>(word, nframes, kind) : 0u;
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t m = i < nwords ? class_word_mask<N>(word0 + i, nframes, kind) : 0u;
     const uint32_t s = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(m));
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(&s_sum, s);
     __syncthreads();
@@ -580,11 +581,12 @@ __global__ void __launch_bounds__(1024) list_scan_kernel(uint32_t *blk, uint32_t
 
 template <int N>
 __global__ void __launch_bounds__(256) list_write_kernel(const uint32_t *blk, uint64_t *list, uint64_t cap,
-                                                         uint64_t nwords, uint64_t nframes, int kind,
-                                                         int32_t *status) {
+                                                         uint64_t word0, uint64_t nwords, uint64_t nframes,
+                                                         int kind, int32_t *status) {
     __shared__ uint32_t s_warp[8];
-    const uint64_t word = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t m = word < nwords ? class_word_mask<N>(word, nframes, kind) : 0u;
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t word = word0 + i;
+    const uint32_t m = i < nwords ? class_word_mask<N>(word, nframes, kind) : 0u;
     const uint32_t c = (uint32_t)__popc(m);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // inclusive warp prefix of c
@@ -850,29 +852,36 @@ void launch_layer_n(int n, const LayerArgs &a, int block, int units, cudaStream_
     }
 }
 
-// List of kind c at N worlds: S4/S5 filter the T frames, K4 the K frames.
+// List of kind c at N worlds: S4/S5 filter the T frames, K4 the K frames,
+// those in frame words [w0, w1) of the scanned enumeration (a census whose
+// K-index window leaves out the rest lists only the window's words).
 template <int N>
-void launch_list(uint8_t *ws, const ListPlan &p, int c, int32_t *status, cudaStream_t s) {
+void launch_list(uint8_t *ws, const ListPlan &p, int c, int32_t *status, cudaStream_t s, uint64_t w0,
+                 uint64_t w1) {
     const uint64_t nf = c == LIST_K4 ? (1ull << (N * N)) : t_frames(N);
-    const uint64_t nw = (nf + 31) / 32;
-    const unsigned nb = (unsigned)((nw + 255) / 256);
+    const uint64_t all = (nf + 31) / 32;
+    if (w1 > all) w1 = all;
+    if (w0 > w1) w0 = w1;
+    const uint64_t nw = w1 - w0;
+    const unsigned nb = (unsigned)((nw + 255) / 256 > 0 ? (nw + 255) / 256 : 1);
     uint32_t *blk = (uint32_t *)(ws + p.blk_off);
     uint64_t *len = (uint64_t *)(ws + p.len_off[c][N]);
     uint64_t *list = (uint64_t *)(ws + p.list_off[c][N]);
     const uint64_t cap = list_cap(c, N);
-    list_count_kernel<N><<<nb, 256, 0, s>>>(blk, nw, nf, c);
+    list_count_kernel<N><<<nb, 256, 0, s>>>(blk, w0, nw, nf, c);
     list_scan_kernel<<<1, 1024, 0, s>>>(blk, nb, len);
-    list_write_kernel<N><<<nb, 256, 0, s>>>(blk, list, cap, nw, nf, c, status);
+    list_write_kernel<N><<<nb, 256, 0, s>>>(blk, list, cap, w0, nw, nf, c, status);
 }
 
-void launch_list_n(int n, uint8_t *ws, const ListPlan &p, int c, int32_t *status, cudaStream_t s) {
+void launch_list_n(int n, uint8_t *ws, const ListPlan &p, int c, int32_t *status, cudaStream_t s,
+                   uint64_t w0 = 0, uint64_t w1 = ~0ull) {
     switch (n) {
-    case 1: launch_list<1>(ws, p, c, status, s); break;
-    case 2: launch_list<2>(ws, p, c, status, s); break;
-    case 3: launch_list<3>(ws, p, c, status, s); break;
-    case 4: launch_list<4>(ws, p, c, status, s); break;
-    case 5: launch_list<5>(ws, p, c, status, s); break;
-    case 6: launch_list<6>(ws, p, c, status, s); break;
+    case 1: launch_list<1>(ws, p, c, status, s, w0, w1); break;
+    case 2: launch_list<2>(ws, p, c, status, s, w0, w1); break;
+    case 3: launch_list<3>(ws, p, c, status, s, w0, w1); break;
+    case 4: launch_list<4>(ws, p, c, status, s, w0, w1); break;
+    case 5: launch_list<5>(ws, p, c, status, s, w0, w1); break;
+    case 6: launch_list<6>(ws, p, c, status, s, w0, w1); break;
     }
 }
 
@@ -951,10 +960,16 @@ extern "C" int mk_census(const mk_program *d_progs, int32_t nprog, const mk_cens
     const int depth = cfg->max_depth ? cfg->max_depth : MK_MAX_STACK;
     const int units = cfg->tune.units ? cfg->tune.units : 8;
 
-    // class lists for S4 / S5 / K4
+    // class lists for S4 / S5 / K4, over the words of the K-index window
+    // (K4 scans K frames by index, S4/S5 T frames by compact index, which is
+    // monotone in the K index)
     for (int c = 0; c < NLISTS; ++c) {
         if (!(cfg->classes & list_class_bit(c))) continue;
-        for (int n = cfg->n_min; n <= cfg->n_max; ++n) launch_list_n(n, ws, plan, c, d_status, s);
+        for (int n = cfg->n_min; n <= cfg->n_max; ++n) {
+            uint64_t w0, w1;
+            layer_words(cfg, c == LIST_K4 ? 0 : 1, n, &w0, &w1);
+            launch_list_n(n, ws, plan, c, d_status, s, w0, w1);
+        }
     }
 
     int ci = 0;
