@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--impl", default="mk", choices=["mk", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="census line only (by default it also carries short runs of the separation "
+                         "search and the uneven batch, measured after the census)")
     ap.add_argument("--profile-case", default=None,
                     help="matched:R -- row R of --workload matched, twice; uneven:F -- the first F "
                          "formulas of the uneven batch, one persistent launch twice; "
@@ -363,6 +366,8 @@ def run_mk(args):
         import oracle
         out["cpu_baseline"] = {"value": e / s / 1e9, "unit": UNIT, "cores": oracle.threads(),
                                "kind": "oracle", "sample": desc}
+    if world == 1 and not args.no_secondary:
+        out["secondary"] = secondary_results()
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -388,7 +393,11 @@ def run_uneven(args):
     mkbuild.build()
     dev = torch.device("cuda", 0)
     items = W.uneven_formulas(3)
-    tune = E.autotune_uneven(items, samples=64, seed=3, use_cache=False)
+    if getattr(args, "quick", False):
+        # inside the census bench line: the tune the autotuner chooses on a GB300
+        tune = {"units": 4, "block": 128, "tiles": [16, 16, 8, 16]}
+    else:
+        tune = E.autotune_uneven(items, samples=64, seed=3, use_cache=False)
     job = E.UnevenJob(items, samples=64, seed=3, tiles=tune["tiles"],
                       tune={"units": tune["units"], "block": tune["block"]})
     job.launch()
@@ -441,10 +450,12 @@ def run_uneven(args):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
     evals = job.evals()
-    ops = 0.0
+    ops, ops_src = 0.0, 0.0
     for (t, c, nmax), p in zip(items, job.progs):
         for n in range(1, nmax + 1):
-            ops += E.mk.class_frames(c, n) * E.n_valuations(int(p["nvars"]), n, 64) * E.lop3_per_eval(p, n)
+            units = E.mk.class_frames(c, n) * E.n_valuations(int(p["nvars"]), n, 64)
+            ops += units * E.lop3_per_eval(p, n)
+            ops_src += units * E.source_ops_per_eval(t, n)
     peak = 152 * LOP3_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
     out = {"metric": METRIC, "value": evals / (ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -462,12 +473,15 @@ def run_uneven(args):
                         "traffic": DRAM_BYTES_PER_FORMULA_UNEVEN * len(items),
                         "traffic_note": "bytes per launch, scaled by formulas from a 2,000-formula ncu capture "
                                         "(bench.py --profile-case uneven:2000)",
-                        "note": "step time (graph replay) in the denominator"},
+                        "note": "step time (graph replay) in the denominator",
+                        "basis": "compiled programs: (n*#Boolean + n^2*#modal + n)/32 per evaluation",
+                        "frac_survey": ops_src / (ms / 1e3) / 1e12 / peak,
+                        "basis_survey": "the same count on the source formulas"},
            "e2e": {"value": evals / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
                    "h2d_bytes_per_step": sum(h.numel() * h.element_size() for h in h_in),
                    "d2h_bytes_per_step": h_out.numel() * 8},
            "clocks": clk}
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def separation_ops(pair, n, progs=None):
@@ -544,7 +558,7 @@ def run_separation(args):
     job6 = E.SeparateJob([pairs[i] for i in six], 6, 6, seed=4)
     job6.launch()
     torch.cuda.synchronize()
-    e6 = [_events() for _ in range(2)]
+    e6 = [_events() for _ in range(1 if getattr(args, "quick", False) else 2)]
     for a, b in e6:
         a.record()
         job6.launch()
@@ -627,7 +641,34 @@ def run_separation(args):
                                "kind": "oracle",
                                "sample": "oracle.pair_layer on %d (pair, 2^18 six-world frames) windows of the "
                                          "pairs that reach six worlds" % units}
-    print(json.dumps(out), flush=True)
+    return out
+
+
+def secondary_results():
+    """The separation search and the uneven batch, measured after the census
+    in the same process (short runs; a failure is recorded, not raised), so
+    that the census bench line also carries them."""
+    import types
+    res = {}
+    runs = (("separation", run_separation, 1, 1), ("uneven", run_uneven, 3, 2))
+    keep = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "certified_splits",
+            "speedup_vs_per_bucket", "per_bucket_plain_launches", "gpu_launches", "clocks")
+    for name, fn, steps, warmup in runs:
+        try:
+            r = fn(types.SimpleNamespace(steps=steps, warmup=warmup, no_cpu_baseline=True, cpu_seconds=0.0,
+                                         quick=True))
+            d = {k: r[k] for k in keep if k in r}
+            d["workload"] = r["config"]["workload"]
+            if "splits_by_n" in r["config"]:
+                d["splits_by_n"] = r["config"]["splits_by_n"]
+            rf = r["roofline"]
+            d["roofline"] = {k: rf[k] for k in ("kernel", "achieved", "peak", "unit", "frac", "frac_survey",
+                                                 "basis", "traffic") if k in rf}
+            d["e2e"] = r["e2e"]
+            res[name] = d
+        except Exception as e:          # keep the census line whatever happens here
+            res[name] = {"error": repr(e)[:400]}
+    return res
 
 
 def run_adversarial(args):
@@ -1116,9 +1157,9 @@ def main():
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "uneven":
-        run_uneven(args)
+        print(json.dumps(run_uneven(args)), flush=True)
     elif args.workload == "separation":
-        run_separation(args)
+        print(json.dumps(run_separation(args)), flush=True)
     elif args.workload == "learned":
         run_learned(args)
     elif args.workload == "adversarial":
