@@ -395,7 +395,7 @@ def run_uneven(args):
     items = W.uneven_formulas(3)
     if getattr(args, "quick", False):
         # inside the census bench line: the tune the autotuner chooses on a GB300
-        tune = {"units": 4, "block": 128, "tiles": [16, 16, 8, 16]}
+        tune = dict(E.UNEVEN_TUNE)
     else:
         tune = E.autotune_uneven(items, samples=64, seed=3, use_cache=False)
     job = E.UnevenJob(items, samples=64, seed=3, tiles=tune["tiles"],

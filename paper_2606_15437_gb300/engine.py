@@ -194,6 +194,10 @@ def gather_census_plan(plan, nprog, classes=CLASSES, n_min=1, n_max=5):
     return out
 
 
+# The uneven batch's launch configuration as the autotuner chooses it on a
+# GB300 (units, CTA size, formulas per tile of the four length buckets).
+UNEVEN_TUNE = {"units": 4, "block": 128, "tiles": [16, 16, 8, 16]}
+
 # The separation workload's search: every frame of 1..6 worlds, then 1e8
 # sampled relations of 7 and 8 worlds (seed 4) for pairs still unsplit.
 SEPARATION_SEARCH = dict(n_exh_min=1, n_exh_max=6, n_smp_min=7, n_smp_max=8, frames_per_n=100_000_000, seed=4)

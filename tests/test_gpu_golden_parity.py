@@ -156,7 +156,8 @@ def test_uneven_batch_larger_layers_equal_the_oracle():
     items = W.uneven_formulas(3)
     sha = hashlib.sha256("\n".join("%s\t%s\t%d" % it for it in items).encode()).hexdigest()
     assert G.header_values(name)["items_sha256"] == sha
-    job = E.UnevenJob(items, samples=64, seed=3)
+    t = E.UNEVEN_TUNE
+    job = E.UnevenJob(items, samples=64, seed=3, tiles=tuple(t["tiles"]), tune={"units": t["units"], "block": t["block"]})
     job.launch()
     res = job.results().copy()
     want = G.census_rows(name)

@@ -112,3 +112,22 @@ def test_sampled_six_world_split_certifies():
         if want != mk.NO_KEY:
             assert mk.split_sampled(got[i]) and mk.split_n(got[i]) in (6, 7)
             assert mk.certify_struct(job.certificate(i, got[i])) == 1
+
+
+def test_unaligned_window_first_splits():
+    """A K-index window that starts and ends inside frame words (the search
+    rounds its first word down to a multiple of its unit count and masks the
+    frames before frame_lo): first splits within the window equal the
+    oracle's, for pairs splitting early, late and not at all in it."""
+    pairs = [(W.alpha(1), W.alpha(2)), ("<><>T", "<>[]T"), ("[]<>[]F", "[][]F"), ("[]F", "~<>T"),
+             ("<>(<>T & []F)", "<>[]F")] + W.separation_pairs()[32:60]
+    for n, lo, hi in ((4, 333, 40001), (5, 12345, 12345 + 70000), (5, 2 ** 25 - 9999, 2 ** 25)):
+        job = engine().SeparateJob(pairs, n, n, frame_lo=lo, frame_hi=hi)
+        got = job.run()
+        for i, (a, b) in enumerate(pairs):
+            r = oracle.pair_layer(a, b, n, f_lo=lo, f_hi=hi)
+            want = mk.NO_KEY
+            if r["split"]:
+                f, v, w, _, _ = r["split"]
+                want = mk.split_key(False, n, f, v, w)
+            assert int(got[i]) == want, (a, b, n, lo)
