@@ -131,3 +131,30 @@ def test_unaligned_window_first_splits():
                 f, v, w, _, _ = r["split"]
                 want = mk.split_key(False, n, f, v, w)
             assert int(got[i]) == want, (a, b, n, lo)
+
+
+def _balanced(d, a, b):
+    """A balanced &/| tree of depth d over the leaves a, b: its postfix
+    program needs d stack entries."""
+    if d == 0:
+        return a
+    x, y = _balanced(d - 1, a, b), _balanced(d - 1, b, a)
+    return "(%s %s %s)" % (x, "&" if d % 2 else "|", y)
+
+
+def test_deepest_stack_and_empty_batch():
+    """Programs that need every stack entry (MK_MAX_STACK = 4) size the
+    search's shared-memory stack; their first splits through four worlds
+    equal the oracle's.  An empty batch returns nothing and launches
+    nothing."""
+    deep = _balanced(4, "<>p", "[]q")
+    assert mk.compile(deep).depth == 4
+    pairs = [(deep, _balanced(4, "[]q", "<>p")), (deep, _balanced(3, "<>p", "[]q")),
+             (_balanced(3, "<>p", "[]q"), "<>p & []q"), (deep, deep.replace("[]q", "<>q"))]
+    job = engine().SeparateJob(pairs, 1, 4, samples=16, seed=5)
+    assert job.cfg.max_depth == 4
+    got = job.run()
+    for i, (a, b) in enumerate(pairs):
+        want = oracle_first_split(a, b, (1, 2, 3, 4), job.sample_table)
+        assert int(got[i]) == want, (a, b)
+    assert len(engine().SeparateJob([], 1, 3).run()) == 0
