@@ -153,3 +153,51 @@ def test_learned_proposal_gain():
     print("certified per 1e12 evals: mlp %.3f, random among identical-vector pairs %.3f, random %.3f" % (
         r["mlp"]["certified_per_1e12_evals"], r["random_identical"]["certified_per_1e12_evals"],
         r["random"]["certified_per_1e12_evals"]))
+
+
+def test_learned_workload_full_size_sampled_outputs():
+    """The learned-proposal workload at its full size (10,000 formulas,
+    4,096 pointed models, 1,024-NN universe of 5,467,766 pairs), checked on
+    sampled outputs the references can compute one by one: truth-vector bits
+    against the oracle's evaluation of the model, neighbour lists against
+    brute-force Hamming distances over all 10,000 vectors, and BF16 scores of
+    universe pairs against float64 with the same BF16-rounded weights."""
+    E_ = E()
+    texts = W.proposal_formulas(5, 10000)
+    models, groups = W.pointed_models(5)
+    bits = E_.truth_vectors(texts, models=models, groups=groups)
+    bits_np = bits.cpu().numpy().view(np.uint32)
+    assert bits_np.shape == (10000, len(models) // 32) and len(models) == 4096
+    rng = np.random.default_rng(17)
+    for i, j in zip(rng.integers(0, 10000, 300), rng.integers(0, 4096, 300)):
+        m = models[j]
+        n = int(m["n"])
+        R = oracle.frame_matrix(int(m["frame"]), n)
+        V = np.array([[(int(m["val"]) >> (v * n + w)) & 1 for w in range(n)] for v in range(4)], np.uint8)
+        assert ((int(bits_np[i, j // 32]) >> (j % 32)) & 1) == oracle.eval_model(texts[i], R, V)[int(m["world"])]
+    k = 1024
+    nbr, dist = E_.hamming_knn(bits, k)
+    pop = np.unpackbits(bits_np.view(np.uint8), axis=1)
+    for q in rng.integers(0, 10000, 4):
+        d = (pop ^ pop[q]).sum(1)
+        d[q] = 1 << 30
+        kth = np.sort(d)[k - 1]
+        got = nbr[q]
+        assert np.array_equal(np.sort(d[got]), np.sort(d)[:k])           # the k least distances
+        assert (d[got] <= kth).all() and len(set(got.tolist())) == k and q not in got
+        assert np.array_equal(dist[q].astype(np.int64), d[got])
+    pa, pb = E_.knn_universe(nbr, 5_467_766, 5)
+    assert len(pa) == 5_467_766
+    F, H = bits_np.shape[1] * 64, 256
+    net = E_.MLP(F, H, seed=6)
+    pick = rng.integers(0, len(pa), 512)
+    tpa = torch.from_numpy(pa[pick]).cuda()
+    tpb = torch.from_numpy(pb[pick]).cuda()
+    s = net.score(bits, tpa, tpb).cpu().numpy()
+    params = net.params.cpu().numpy().astype(np.float64)
+    w1 = torch.from_numpy(params[:F * H].astype(np.float32)).to(torch.bfloat16).float().numpy()
+    p2 = params.copy()
+    p2[:F * H] = w1
+    zr = ref.forward(p2, F, H, bits_np, pa[pick], pb[pick])
+    # FP32 sums over 8,192 features: the F = 256 tolerance widened by sqrt(8192 / 256)
+    assert np.abs(s - zr).max() <= 1e-3 * np.sqrt(F / 256) * max(1.0, float(np.abs(zr).max()))
