@@ -157,8 +157,8 @@ __global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
     uint32_t *s_rows = (uint32_t *)(smem + SM::code_bytes(tile) + SM::meta_bytes(tile));
     uint32_t *s_stack = (uint32_t *)((uint8_t *)s_rows + SM::row_bytes()) + threadIdx.x;
 
-    const uint64_t strip_words = (uint64_t)BLOCK * U;
-    const uint64_t cta_word0 = a.word_lo + (uint64_t)blockIdx.x * a.groups * strip_words;
+    const uint64_t group_words = (uint64_t)BLOCK * U;   // frame words of one group (U per thread)
+    const uint64_t cta_word0 = a.word_lo + (uint64_t)blockIdx.x * a.groups * group_words;
     if (cta_word0 >= a.word_hi) return;
     const unsigned long long floor_key = split_key(a.sampled, N, cta_word0 << 5, 0, 0);
     if (threadIdx.x == 0) s_active = 0;
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(BLOCK) separate_kernel(SepArgs a) {
     int rows_kind = -1;
     uint32_t rows_c0 = 0;
     for (int g = 0; g < a.groups; ++g) {
-        const uint64_t gw0 = cta_word0 + (uint64_t)g * strip_words;
+        const uint64_t gw0 = cta_word0 + (uint64_t)g * group_words;
         if (gw0 >= a.word_hi) break;                       // uniform
         uint32_t E[U][N * N];
         uint32_t valid[U];

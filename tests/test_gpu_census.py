@@ -310,3 +310,22 @@ def test_k4_window_of_table4_matched_row():
     for i, t in enumerate(["F", r["text"], "[]p -> p"]):
         want = oracle.census(t, "K4", 5, f_lo=r["lo"], f_hi=r["hi"])
         assert tuple(int(x) for x in res[i, 0, 0]) == (want["cm_count"], want["frames_refuted"], oracle_key(want))
+
+
+def test_matched_rows_equal_the_oracle_at_full_shape():
+    """Every matched single-formula row (Table 1, Table 4, Sec. 8) as the
+    matched bench launches it -- one formula on its K-index window, every
+    valuation, the valuations split over CTAs where the frames cannot fill
+    the GPU -- against the oracle on the same window; the Sec. 8 stress row
+    (3.4e10 evaluations) on its first 2,048 frames."""
+    E = engine()
+    for r in W.matched_rows():
+        lo, hi = r["lo"], r["hi"]
+        if r["frames"] * r["valuations"] > 3e8:
+            hi = lo + 2048
+        job = E.CensusJob([r["text"]], (r["cls"],), 5, 5, samples=0, frame_lo=lo, frame_hi=hi)
+        got = tuple(int(x) for x in job.run()[0, 0, 0])
+        want = oracle.census(r["text"], r["cls"], 5, f_lo=lo, f_hi=hi)
+        assert got == (want["cm_count"], want["frames_refuted"], oracle_key(want)), r["name"]
+        if got[2] != mk.NO_KEY:
+            assert mk.certify_struct(job.certificate(0, r["cls"], 5, got[2])) == 1, r["name"]
