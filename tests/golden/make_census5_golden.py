@@ -9,14 +9,16 @@ Sec. 2 over explicit relations, the corpus scan of Alg. 1 in Sec. 4); the
 inputs come from the seeded generators of ``workloads``.  Nothing of the CUDA
 path is imported.
 
-Two files:
+Three files:
 
 * ``census5_n1to4.tsv.gz`` -- every formula, every class, n = 1..4;
 * ``census5_n5_subset.tsv`` -- full five-world layers (all 2^25 K frames,
   2^20 T frames, the 6,942 S4 and 52 S5 frames) for a stratified subset:
   per variable count k = 0..3 the longest formula and the deepest of the
   longest, seeded random picks (40 / 20 / 2 / 2 for k = 0 / 1 / 2 / 3), and
-  the three axioms.
+  the three axioms;
+* ``census5_n5_k0.tsv`` -- the same full five-world layers for every
+  variable-free formula of the batch (one valuation per frame).
 
 Rows: formula index, class, n, cm_count, frames_refuted, witness as
 "frame,valuation,world" (K index; valuation index or sample slot; least
@@ -28,6 +30,7 @@ resumes from its partial file):
 
     python tests/golden/make_census5_golden.py --part n1to4
     python tests/golden/make_census5_golden.py --part n5
+    python tests/golden/make_census5_golden.py --part n5k0
 """
 import argparse
 import gzip
@@ -146,7 +149,7 @@ def run(texts, units, partial, log_every=200):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--part", choices=("n1to4", "n5"), required=True)
+    ap.add_argument("--part", choices=("n1to4", "n5", "n5k0"), required=True)
     ap.add_argument("--workdir", default=HERE, help="where the resumable partial file lives")
     args = ap.parse_args()
     texts = W.census5_formulas(SEED)
@@ -158,6 +161,17 @@ def main():
         out = os.path.join(HERE, "census5_n1to4.tsv.gz")
         with gzip.open(out, "wt") as f:
             f.write("\n".join(header(texts, "every formula, classes K/T/S4/S5, n = 1..4")) + "\n")
+            for u in units:
+                f.write(rows[u] + "\n")
+    elif args.part == "n5k0":
+        k0 = [p for p in range(len(texts)) if oracle.nvars(texts[p]) == 0]
+        units = [(p, c, 5) for p in k0 for c in CLASSES]
+        partial = os.path.join(args.workdir, "census5_n5_k0.partial")
+        rows = run(texts, units, partial, log_every=200)
+        out = os.path.join(HERE, "census5_n5_k0.tsv")
+        with open(out, "w") as f:
+            f.write("\n".join(header(texts, "full n = 5 layers of every variable-free formula (%d)" % len(k0)))
+                    + "\n")
             for u in units:
                 f.write(rows[u] + "\n")
     else:

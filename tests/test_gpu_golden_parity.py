@@ -172,3 +172,18 @@ def test_uneven_batch_larger_layers_equal_the_oracle():
     job.capture()
     job.replay()
     assert np.array_equal(job.results(), res)
+
+
+def test_census_batch_variable_free_five_world_layers_equal_the_oracle(census5):
+    """Every variable-free formula of the batch (one valuation per frame): its
+    full five-world K, T, S4 and S5 layers against the oracle's stored results."""
+    name = "census5_n5_k0.tsv"
+    _need(name)
+    texts, progs, _, res = census5
+    assert G.header_values(name)["texts_sha256"] == hashlib.sha256("\n".join(texts).encode()).hexdigest()
+    want = G.census_rows(name)
+    k0 = [p for p in range(len(texts)) if int(progs[p]["nvars"]) == 0]
+    assert sorted({p for p, _, _ in want}) == k0 and len(want) == 4 * len(k0)
+    bad = [(p, c) for (p, c, n), (cm, fr, w) in want.items()
+           if tuple(int(x) for x in res[p, CLS.index(c), n - 1]) != (cm, fr, _key(w))]
+    assert not bad, bad[:5]
