@@ -38,7 +38,7 @@ constexpr int AT_BLOCK = 256;
 constexpr int AT_U = 4;
 constexpr int AT_ROW_CAP = 64;               // valuation words staged at a time
 constexpr int AT_OPS_STRIDE = MK_MAX_CODE + 2;
-constexpr int AT_TILE = 16;
+constexpr int AT_TILE = 4;                  // formulas per CTA: short CTAs, a fuller grid
 
 struct AtlasArgs {
     const mk_program *progs;
@@ -68,6 +68,13 @@ __device__ __forceinline__ uint32_t lane_atom_word(uint32_t q, int idx) {
     return b < 5 ? lane_pattern(b) : bit_word((uint64_t)q << 5, b);
 }
 
+// Formulas whose valuations on n worlds number at most 8 (k*n <= 3, the
+// variable-free and, at n = 2 or 3, the one-variable ones) would fill only
+// 1-8 of a word's 32 valuation lanes; they are counted by
+// atlas_packed_kernel instead, whose word holds 4 frames x 8 valuations.
+template <int N>
+__device__ __forceinline__ bool atlas_packed(int k) { return N >= 2 && k * N <= 3; }
+
 template <int N, int U, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) atlas_kernel(AtlasArgs a) {
     using SM = AtlasSmem<N, U, BLOCK>;
@@ -90,6 +97,8 @@ __global__ void __launch_bounds__(BLOCK) atlas_kernel(AtlasArgs a) {
             if (p.nvars * N > 16) {
                 nin = -1;
                 if (blockIdx.x == 0) atomicOr(a.status, (int)MK_ST_LIMIT);
+            } else if (atlas_packed<N>(p.nvars)) {
+                nin = -1;                              // counted by atlas_packed_kernel
             }
         } else if (blockIdx.x == 0) {
             atomicOr(a.status, (int)MK_ST_PROGRAM);
@@ -138,6 +147,66 @@ __global__ void __launch_bounds__(BLOCK) atlas_kernel(AtlasArgs a) {
             }
         }
         if (f < a.nframes) a.counts[(size_t)(p0 + fi) * a.ld + f] = cnt;
+    }
+}
+
+// The counts of the formulas with at most 8 valuations per frame.  Lane l
+// of word q holds frame 4q + (l >> 3) under valuation l & 7: frame-index
+// bits 0 and 1 are lane bits 3 and 4 (lane patterns), the higher ones are
+// the same for the whole word, and atom p_0 at world w is valuation bit w,
+// a lane pattern too (k*n <= 3, so no valuation bit beyond bit 2).  One
+// program run covers 4 frames under all their valuations; lanes of unused
+// valuations are masked.  Needs N >= 2 (at least 4 frames).
+template <int N, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) atlas_packed_kernel(AtlasArgs a) {
+    constexpr int RW = RowShape<N>::WORDS;
+    constexpr int RS = RowShape<N>::RS;
+    __shared__ uint16_t s_offs[AT_TILE * AT_OPS_STRIDE];
+    __shared__ uint8_t s_ops[AT_TILE * AT_OPS_STRIDE];
+    __shared__ int s_nin[AT_TILE], s_k[AT_TILE];
+    __shared__ __align__(16) uint32_t s_row[RW];
+    extern __shared__ __align__(16) uint32_t s_pstack[];       // MK_MAX_STACK x N words per thread
+    static_assert(N >= 2, "four frames per word");
+
+    const int p0 = blockIdx.y * AT_TILE;
+    const int np = min(AT_TILE, a.nprog - p0);
+    for (int i = threadIdx.x; i < np; i += BLOCK) {
+        const mk_program &p = a.progs[p0 + i];
+        const int nin = program_ok(p) && atlas_packed<N>(p.nvars) ? p.n_instr : -1;
+        s_nin[i] = nin;
+        s_k[i] = p.nvars;
+        if (nin >= 0) decode_program<N, 1, BLOCK, false>(p, s_ops + i * AT_OPS_STRIDE, s_offs + i * AT_OPS_STRIDE);
+    }
+    for (int i = threadIdx.x; i < RW; i += BLOCK) {
+        const int v = i / RS, w = i % RS, b = v * N + w;
+        s_row[i] = (w < N && b < 3) ? lane_pattern(b) : 0u;
+    }
+    __syncthreads();
+
+    const uint64_t q = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;   // word: frames 4q .. 4q+3
+    const uint64_t nwords = a.nframes / 4;
+    uint32_t E[1][N * N];
+#pragma unroll
+    for (int e = 0; e < N * N; ++e) E[0][e] = e < 2 ? lane_pattern(3 + e) : bit_word(q << 2, e);
+    if (q >= nwords) return;                                         // no barrier follows
+    for (int fi = 0; fi < np; ++fi) {
+        if (s_nin[fi] < 0) continue;
+        const uint32_t nval = 1u << (s_k[fi] * N);                   // 1, 4 or 8
+        const uint32_t vmask = nval >= 8 ? 0xFFFFFFFFu : 0x01010101u * ((1u << nval) - 1u);
+        uint32_t A[1][N];
+        run_program<N, 1, 1, BLOCK, 0, false>(s_ops + fi * AT_OPS_STRIDE, s_offs + fi * AT_OPS_STRIDE, s_row, E,
+                                              s_pstack + threadIdx.x, A);
+        uint32_t bad[N];
+#pragma unroll
+        for (int w = 0; w < N; ++w) bad[w] = ~A[0][w] & vmask;
+        uint32_t *out = a.counts + (size_t)(p0 + fi) * a.ld + 4 * q;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            uint32_t c = 0;
+#pragma unroll
+            for (int w = 0; w < N; ++w) c += __popc(bad[w] & (0xFFu << (8 * g)));
+            out[g] = c;
+        }
     }
 }
 
@@ -372,6 +441,15 @@ void launch_atlas(const AtlasArgs &a, cudaStream_t s) {
     ensure_dynamic_smem((const void *)kern, SM::total());
     dim3 grid((unsigned)((a.nframes + AT_BLOCK - 1) / AT_BLOCK), (unsigned)((a.nprog + AT_TILE - 1) / AT_TILE));
     kern<<<grid, AT_BLOCK, SM::total(), s>>>(a);
+    if constexpr (N >= 2) {
+        constexpr int PB = 128;
+        const uint64_t nwords = a.nframes / 4;
+        const size_t stack = (size_t)MK_MAX_STACK * N * PB * 4;
+        auto pk = atlas_packed_kernel<N, PB>;
+        ensure_dynamic_smem((const void *)pk, stack);
+        dim3 pgrid((unsigned)((nwords + PB - 1) / PB), (unsigned)((a.nprog + AT_TILE - 1) / AT_TILE));
+        pk<<<pgrid, PB, stack, s>>>(a);
+    }
 }
 
 int32_t pow2_at_least(int32_t n) {
