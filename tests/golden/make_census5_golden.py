@@ -9,7 +9,7 @@ Sec. 2 over explicit relations, the corpus scan of Alg. 1 in Sec. 4); the
 inputs come from the seeded generators of ``workloads``.  Nothing of the CUDA
 path is imported.
 
-Three files:
+Four files:
 
 * ``census5_n1to4.tsv.gz`` -- every formula, every class, n = 1..4;
 * ``census5_n5_subset.tsv`` -- full five-world layers (all 2^25 K frames,
@@ -18,7 +18,10 @@ Three files:
   longest, seeded random picks (40 / 20 / 2 / 2 for k = 0 / 1 / 2 / 3), and
   the three axioms;
 * ``census5_n5_k0.tsv`` -- the same full five-world layers for every
-  variable-free formula of the batch (one valuation per frame).
+  variable-free formula of the batch (one valuation per frame);
+* ``census5_n5_extra.tsv`` -- the same for a further seeded sample of
+  formulas with variables outside the subset: 60 with one variable, 10 with
+  two and 10 with three (the sampled valuations of S = 256).
 
 Rows: formula index, class, n, cm_count, frames_refuted, witness as
 "frame,valuation,world" (K index; valuation index or sample slot; least
@@ -31,6 +34,7 @@ resumes from its partial file):
     python tests/golden/make_census5_golden.py --part n1to4
     python tests/golden/make_census5_golden.py --part n5
     python tests/golden/make_census5_golden.py --part n5k0
+    python tests/golden/make_census5_golden.py --part n5extra
 """
 import argparse
 import gzip
@@ -149,7 +153,7 @@ def run(texts, units, partial, log_every=200):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--part", choices=("n1to4", "n5", "n5k0"), required=True)
+    ap.add_argument("--part", choices=("n1to4", "n5", "n5k0", "n5extra"), required=True)
     ap.add_argument("--workdir", default=HERE, help="where the resumable partial file lives")
     args = ap.parse_args()
     texts = W.census5_formulas(SEED)
@@ -163,6 +167,25 @@ def main():
             f.write("\n".join(header(texts, "every formula, classes K/T/S4/S5, n = 1..4")) + "\n")
             for u in units:
                 f.write(rows[u] + "\n")
+    elif args.part == "n5extra":
+        subset = set(n5_subset(texts))
+        rng = random.Random(11)
+        extra = []
+        for k, count in ((1, 60), (2, 10), (3, 10)):
+            idx = [p for p in range(len(texts)) if oracle.nvars(texts[p]) == k and p not in subset]
+            extra += rng.sample(idx, count)
+        extra.sort()
+        units = [(p, c, 5) for p in extra for c in ("S5", "S4", "T", "K")]
+        units.sort(key=lambda u: (u[1] == "K", oracle.nvars(texts[u[0]]), W.nodes(texts[u[0]])))
+        partial = os.path.join(args.workdir, "census5_n5_extra.partial")
+        rows = run(texts, units, partial, log_every=10)
+        out = os.path.join(HERE, "census5_n5_extra.tsv")
+        with open(out, "w") as f:
+            f.write("\n".join(header(texts, "full n = 5 layers of a further seeded sample of %d formulas with "
+                                     "variables (60 / 10 / 10 with k = 1 / 2 / 3)" % len(extra))) + "\n")
+            for p in extra:
+                for c in CLASSES:
+                    f.write(rows[(p, c, 5)] + "\n")
     elif args.part == "n5k0":
         k0 = [p for p in range(len(texts)) if oracle.nvars(texts[p]) == 0]
         units = [(p, c, 5) for p in k0 for c in CLASSES]
