@@ -41,9 +41,10 @@ SMS = 152
 SM_MAX_MHZ = 2070.0
 LOP3_PER_SM_CLK = 64        # 3-input logic ops per SM per clock (4 SMSPs x 16 ALU lanes)
 # DRAM bytes (read + write) of census_layer_kernel<5, 8, 256> per formula of
-# a K n=5 launch: 88,576 B for the 16-formula ncu capture of this kernel
-# (bench.py --profile-case census5:16), scaled by the formulas processed.
-DRAM_BYTES_PER_FORMULA_K5 = 88576 / 16
+# a K n=5 launch: 980,990 B read and 0 written by the full 5,624-formula
+# launch (bench.py --profile-case census5:5624, a one-pass ncu capture of
+# the two DRAM counters); per formula so other batch sizes scale.
+DRAM_BYTES_PER_FORMULA_K5 = 980990 / 5624
 # DRAM bytes (read + write) of one census_layer_kernel<5, 8, 256, 1> launch of
 # Table 1's matched row (bench.py --profile-case matched:0, ncu capture)
 DRAM_BYTES_MATCHED_T1 = 119296
@@ -354,7 +355,9 @@ def run_mk(args):
                         "basis_source": "source formulas: (n*#Boolean + n^2*#modal + n)/32 per evaluation, "
                                         "operators counted in the formula text",
                         "algorithmic_ops_per_launch_source": ops_src,
-                        "traffic_note": "bytes per launch, scaled from a 16-formula ncu capture",
+                        "traffic_note": "bytes per launch, from an ncu capture of the full launch "
+                                        "(0.98 MB read, 0 written; programs 0.59 MB and results 0.13 MB "
+                                        "are the algorithmic bytes)",
                         "algorithmic_ops_per_launch": ops_dom, "launch_ms": dom_ms,
                         "peak_basis": "%d SMs x %d logic ops/clk x %.0f MHz" % (sms, LOP3_PER_SM_CLK, SM_MAX_MHZ),
                         "calibrated_lop3_tops": cal_tops},
