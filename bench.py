@@ -53,12 +53,13 @@ DRAM_BYTES_MATCHED_T1 = 119296
 DRAM_BYTES_PER_PAIR_MLP = (10058240 + 24808704) / 77824
 # stress_kernel<12, 2, 1, 8, 256> on 2^16 relations: 1.34 MB read, 0 written
 DRAM_BYTES_PER_RELATION_STRESS = 1339392 / 65536
-# census_queue_kernel<5, 4, 128> on 2,000 uneven-batch formulas: 1.41 MB read
-DRAM_BYTES_PER_FORMULA_UNEVEN = 1411840 / 2000
-# separate_kernel<6, 4, 256, 0> on one 2^27-frame chunk of 64 of the bench's
-# late pairs (ncu capture of the separation6:64 profile case): 93,184 B read,
-# 0 written, per pair staged
-DRAM_BYTES_PER_PAIR_SEPARATION6 = 93184 / 64
+# census_queue_kernel<5, 4, 128>, the full 20,000-job persistent launch
+# (bench.py --profile-case uneven:20000, one ncu pass): 11.82 MB read, 0 written
+DRAM_BYTES_PER_FORMULA_UNEVEN = 11.82e6 / 20000
+# separate_kernel<6, 4, 256, 0> on one 2^27-frame chunk of all 191 pairs the
+# bench's six-world layer searches (bench.py --profile-case separation6:191,
+# one ncu pass): 452.1 KB read, 0 written; per pair staged
+DRAM_BYTES_PER_PAIR_SEPARATION6 = 452100 / 191
 
 
 def parse():
@@ -474,8 +475,8 @@ def run_uneven(args):
            "roofline": {"bound": "alu", "kernel": "census_queue_kernel", "achieved": ops / (ms / 1e3) / 1e12,
                         "peak": peak, "unit": "Tops/s (3-input logic ops)", "frac": ops / (ms / 1e3) / 1e12 / peak,
                         "traffic": DRAM_BYTES_PER_FORMULA_UNEVEN * len(items),
-                        "traffic_note": "bytes per launch, scaled by formulas from a 2,000-formula ncu capture "
-                                        "(bench.py --profile-case uneven:2000)",
+                        "traffic_note": "bytes per launch, from a one-pass ncu capture of the full launch "
+                                        "(bench.py --profile-case uneven:20000)",
                         "note": "step time (graph replay) in the denominator",
                         "basis": "compiled programs: (n*#Boolean + n^2*#modal + n)/32 per evaluation",
                         "frac_source": ops_src / (ms / 1e3) / 1e12 / peak,
@@ -612,8 +613,8 @@ def run_separation(args):
                         "frac": achieved6 / peak_tops,
                         "traffic": None if DRAM_BYTES_PER_PAIR_SEPARATION6 is None
                         else DRAM_BYTES_PER_PAIR_SEPARATION6 * len(six),
-                        "traffic_note": "bytes per launch (one 2^27-frame chunk), scaled by the pairs staged "
-                                        "from an ncu capture of 64 late pairs",
+                        "traffic_note": "bytes per launch (one 2^27-frame chunk of the 191 late pairs), "
+                                        "from a one-pass ncu capture of that launch",
                         "basis": "compiled programs: (n*(#Boolean + n*#modal) of phi and of psi + n)/32 per "
                                  "(pair, frame), after the normal form and constant folding; frames counted "
                                  "up to each pair's first split",
