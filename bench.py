@@ -919,6 +919,39 @@ def run_mlp(args):
     clk = clocks.stop()
     if int(st.item()):
         raise SystemExit("tcgen05 layer reported device status %d" % int(st.item()))
+    # the training step: loss and gradient of one 4,096-pair batch (FP32
+    # SIMT GEMMs: forward through both hidden layers, backward to every
+    # weight; the 0/1 features are generated in the GEMM loader), then Adam
+    TB = 4096
+    y = torch.from_numpy((rng.random(TB) < 0.3).astype(np.float32)).to(dev)
+    tpa, tpb = pa[:TB].contiguous(), pb[:TB].contiguous()
+    ws_t = torch.empty(mk.mlp_train_workspace_size(TB, F, H), dtype=torch.uint8, device=dev)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+
+    def train_step():
+        mk.mlp_gradient_raw(net.params.data_ptr(), F, H, vec.data_ptr(), tpa.data_ptr(), tpb.data_ptr(),
+                            y.data_ptr(), None, TB, net.grad.data_ptr(), loss.data_ptr(), ws_t.data_ptr(),
+                            ws_t.numel(), sp)
+        net.step += 1
+        mk.adam_step_raw(net.params.data_ptr(), net.grad.data_ptr(), net.m.data_ptr(), net.v.data_ptr(), net.n,
+                         1e-3, 0.9, 0.999, 1e-8, net.step, 1.0 / TB, sp)
+    for _ in range(3):
+        train_step()
+    tt = []
+    for _ in range(max(5, args.steps)):
+        ev = _events()
+        ev[0].record()
+        train_step()
+        ev[1].record()
+        torch.cuda.synchronize()
+        tt.append(ev[0].elapsed_time(ev[1]))
+    train_ms = statistics.median(tt)
+    # multiply-adds: forward x.W1 (F*H), h1.W2 (H*H), h2.w3 (H); backward
+    # dW1 = x^T d1 (F*H), dW2 = h1^T d2 (H*H), d1 = d2 W2^T (H*H), dw3 (H)
+    train_flops = 2.0 * TB * (2 * F * H + 3 * H * H + 2 * H)
+    fp32_peak = 152 * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    train_tflops = train_flops / (train_ms / 1e3) / 1e12
+
     flops = 2.0 * B * F * H
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
@@ -935,7 +968,14 @@ def run_mlp(args):
                                         "was still in L2, so writes are a lower bound"},
            "ms": res, "tcgen05_single_group_tflops": flops / (res["tc"] / 1e3) / 1e12,
            "mma_sync_tflops": flops / (res["mma"] / 1e3) / 1e12,
-           "speedup_vs_mma_sync": res["mma"] / res["ws"], "clocks": clk}
+           "speedup_vs_mma_sync": res["mma"] / res["ws"],
+           "training_step": {"pairs": TB, "ms": train_ms, "tflops": train_tflops,
+                             "roofline": {"bound": "fp32 (SIMT)", "kernel": "gemm_f32_kernel (+ head, Adam)",
+                                          "achieved": train_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                                          "frac": train_tflops / fp32_peak,
+                                          "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz"
+                                                        % SM_MAX_MHZ}},
+           "clocks": clk}
     print(json.dumps(out), flush=True)
 
 

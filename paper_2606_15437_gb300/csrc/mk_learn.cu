@@ -182,6 +182,8 @@ __global__ void __launch_bounds__(512) knn_kernel(const uint32_t *bits, int32_t 
 // the first layer's operand can be generated from truth vectors.
 
 constexpr int GBM = 128, GBN = 128, GBK = 8;
+constexpr int kGemmFill = 2 * 152;       // CTAs that fill a GB300 (two per SM)
+constexpr int kGemmMinChunk = 256;       // least K per split-K chunk
 
 enum { A_ROW = 0, A_COL = 1, A_PAIR = 2, A_PAIR_T = 3 };
 enum { B_ROW = 0, B_COL = 1 };
@@ -200,6 +202,8 @@ struct GemmArgs {
     const float *bias;         // per column, may be NULL
     int32_t relu;
     float beta;                // C = acc + beta * C
+    int32_t kchunk;            // split K: CTA z takes k in [z*kchunk, (z+1)*kchunk) (0 = all of K)
+    float *part;               //   and writes its raw sums to part[z][M][N] (the epilogue is later)
 };
 
 template <int AMODE>
@@ -238,15 +242,17 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(GemmArgs g) {
     for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-    for (int k0 = 0; k0 < g.K; k0 += GBK) {
+    const int kb = g.kchunk ? (int)blockIdx.z * g.kchunk : 0;
+    const int ke = g.kchunk ? min(g.K, kb + g.kchunk) : g.K;
+    for (int k0 = kb; k0 < ke; k0 += GBK) {
         // 1024 elements of each tile, 4 per thread
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int e = tid + r * 256;
             const int am = e % GBM, ak = e / GBM;
-            As[ak][am] = load_a<AMODE>(g, m0 + am, k0 + ak);
+            As[ak][am] = k0 + ak < ke ? load_a<AMODE>(g, m0 + am, k0 + ak) : 0.f;
             const int bn = e % GBN, bk = e / GBN;
-            Bs[bk][bn] = load_b<BMODE>(g, k0 + bk, n0 + bn);
+            Bs[bk][bn] = k0 + bk < ke ? load_b<BMODE>(g, k0 + bk, n0 + bn) : 0.f;
         }
         __syncthreads();
 #pragma unroll
@@ -263,6 +269,18 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(GemmArgs g) {
         }
         __syncthreads();
     }
+    if (g.part) {
+        float *pz = g.part + (size_t)blockIdx.z * g.M * g.N;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int m = m0 + tm + i;
+            if (m >= g.M) continue;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (n0 + tn + j < g.N) pz[(size_t)m * g.N + n0 + tn + j] = acc[i][j];
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int m = m0 + tm + i;
@@ -277,6 +295,22 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(GemmArgs g) {
             if (g.relu) v = v > 0.f ? v : 0.f;
             g.C[(size_t)m * g.ldc + n] = v;
         }
+    }
+}
+
+// Split-K epilogue: C = sum_z part[z] (z in order, so the result does not
+// depend on scheduling) + beta * C + bias, then the ReLU.
+__global__ void splitk_epilogue_kernel(const float *part, int32_t S, int32_t M, int32_t N, float *C, int32_t ldc,
+                                       const float *bias, int32_t relu, float beta) {
+    const size_t mn = (size_t)M * N;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < mn; i += (size_t)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        for (int z = 0; z < S; ++z) v += part[(size_t)z * mn + i];
+        const int m = (int)(i / N), n = (int)(i % N);
+        if (beta != 0.f) v += beta * C[(size_t)m * ldc + n];
+        if (bias) v += bias[n];
+        if (relu) v = v > 0.f ? v : 0.f;
+        C[(size_t)m * ldc + n] = v;
     }
 }
 
@@ -306,39 +340,53 @@ __global__ void head_kernel(const float *h2, const float *w3, const float *b3, c
     }
 }
 
-// dh2[p][i] = dz[p] * w3[i] * (h2[p][i] > 0); dw3[i] += sum_p dz[p] h2[p][i]; db3 += sum dz
-__global__ void head_back_kernel(const float *h2, const float *w3, const float *dz, int32_t B, int32_t H,
-                                 float *dh2, float *dw3, float *db3) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < H) {
-        float s = 0.f;
-        for (int p = 0; p < B; ++p) {
-            const float h = h2[(size_t)p * H + i];
-            s += dz[p] * h;
-            dh2[(size_t)p * H + i] = h > 0.f ? dz[p] * w3[i] : 0.f;
-        }
-        dw3[i] = s;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        float s = 0.f;
-        for (int p = 0; p < B; ++p) s += dz[p];
-        db3[0] = s;
-    }
-}
-
 // x *= (h > 0): back through a ReLU whose output is h
 __global__ void relu_back_kernel(float *x, const float *h, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         if (!(h[i] > 0.f)) x[i] = 0.f;
 }
 
-// column sums: out[j] = sum_p x[p][j]
-__global__ void colsum_kernel(const float *x, int32_t B, int32_t H, float *out) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= H) return;
-    float s = 0.f;
-    for (int p = 0; p < B; ++p) s += x[(size_t)p * H + j];
-    out[j] = s;
+// Column sums of X[B][H], each row p optionally scaled by rowscale[p], in
+// two deterministic stages: CTA (x, y) sums rows [y*rows_per, (y+1)*rows_per)
+// of 32 columns (8 warps over interleaved rows, then the 8 warp sums in
+// order) into part[y][H]; colsum_final_kernel adds the chunks in order.
+constexpr int kColChunks = 32;
+__global__ void __launch_bounds__(256) colsum_part_kernel(const float *X, const float *rowscale, int32_t B,
+                                                          int32_t H, int32_t rows_per, float *part) {
+    __shared__ float s[8][33];
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int col = blockIdx.x * 32 + lane;
+    const int r0 = blockIdx.y * rows_per, r1 = min(B, r0 + rows_per);
+    float sum = 0.f;
+    if (col < H)
+        for (int p = r0 + wy; p < r1; p += 8) sum += (rowscale ? rowscale[p] : 1.f) * X[(size_t)p * H + col];
+    s[wy][lane] = sum;
+    __syncthreads();
+    if (wy == 0 && col < H) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t += s[k][lane];
+        part[(size_t)blockIdx.y * H + col] = t;
+    }
+}
+
+__global__ void colsum_final_kernel(const float *part, int32_t R, int32_t H, float *out) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= H) return;
+    float t = 0.f;
+    for (int r = 0; r < R; ++r) t += part[(size_t)r * H + col];
+    out[col] = t;
+}
+
+// dh2[p][i] = dz[p] * w3[i] where h2[p][i] > 0 (back through the head and
+// the second ReLU), element-wise
+__global__ void head_grad_kernel(const float *h2, const float *w3, const float *dz, int32_t B, int32_t H,
+                                 float *dh2) {
+    const size_t n = (size_t)B * H;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int p = (int)(i / H), c = (int)(i % H);
+        dh2[i] = h2[i] > 0.f ? dz[p] * w3[c] : 0.f;
+    }
 }
 
 // Adam (Kingma and Ba, 2015) on n parameters, gradient scaled by gscale
@@ -530,9 +578,26 @@ MlpView mlp_view(float *base, int F, int H) {
 }
 
 template <int AM, int BM>
-void gemm(const GemmArgs &g, cudaStream_t s) {
-    dim3 grid((unsigned)((g.N + GBN - 1) / GBN), (unsigned)((g.M + GBM - 1) / GBM));
+void gemm(const GemmArgs &g0, cudaStream_t s, float *part = nullptr, size_t part_floats = 0) {
+    GemmArgs g = g0;
+    const int ctas = ((g.N + GBN - 1) / GBN) * ((g.M + GBM - 1) / GBM);
+    // a grid below two CTAs per SM splits K (chunks of at least 256, a
+    // multiple of the k step) when the caller gave room for the partials
+    int S = 1;
+    if (part && ctas < kGemmFill && g.K >= 2 * kGemmMinChunk) {
+        S = (kGemmFill + ctas - 1) / ctas;
+        if (S > g.K / kGemmMinChunk) S = g.K / kGemmMinChunk;
+        while (S > 1 && (size_t)S * g.M * g.N > part_floats) --S;
+    }
+    dim3 grid((unsigned)((g.N + GBN - 1) / GBN), (unsigned)((g.M + GBM - 1) / GBM), (unsigned)S);
+    if (S == 1) {
+        gemm_f32_kernel<AM, BM><<<grid, 256, 0, s>>>(g);
+        return;
+    }
+    g.kchunk = ((g.K + S - 1) / S + GBK - 1) / GBK * GBK;
+    g.part = part;
     gemm_f32_kernel<AM, BM><<<grid, 256, 0, s>>>(g);
+    splitk_epilogue_kernel<<<1024, 256, 0, s>>>(part, S, g.M, g.N, g0.C, g0.ldc, g0.bias, g0.relu, g0.beta);
 }
 
 }  // namespace
@@ -569,9 +634,36 @@ extern "C" int mk_mlp_forward(const float *d_params, int32_t features, int32_t h
     return cudaGetLastError() == cudaSuccess ? MK_OK : MK_E_CUDA;
 }
 
+namespace {
+
+// Training workspace beyond the activations: split-K partials (up to
+// kSplitCap copies of the largest GEMM output) and column-sum chunks.
+constexpr size_t kSplitCap = 6;
+
+size_t split_part_floats(int32_t batch, int32_t features, int32_t hidden) {
+    const size_t a = (size_t)batch * hidden, b = (size_t)features * hidden;
+    return kSplitCap * (a > b ? a : b);
+}
+
+size_t train_base_floats(int32_t batch, int32_t features, int32_t hidden) {
+    return (size_t)batch * hidden * 4 + (size_t)batch * 4 + mk_mlp_param_count(features, hidden);
+}
+
+// Deterministic column sums of X[B][H] (rows optionally scaled) into out.
+void colsum(const float *X, const float *rowscale, int32_t B, int32_t H, float *out, float *cpart, cudaStream_t s) {
+    const int rows_per = (B + kColChunks - 1) / kColChunks;
+    const int R = (B + rows_per - 1) / rows_per;
+    colsum_part_kernel<<<dim3((unsigned)((H + 31) / 32), (unsigned)R), 256, 0, s>>>(X, rowscale, B, H, rows_per,
+                                                                                      cpart);
+    colsum_final_kernel<<<(H + 255) / 256, 256, 0, s>>>(cpart, R, H, out);
+}
+
+}  // namespace
+
 extern "C" size_t mk_mlp_train_workspace_size(int32_t batch, int32_t features, int32_t hidden) {
-    return ((size_t)batch * hidden * 4 + (size_t)batch * 4 + mk_mlp_param_count(features, hidden)) * sizeof(float) +
-           1024;
+    if (batch < 1 || features < 1 || hidden < 1) return 0;
+    return (train_base_floats(batch, features, hidden) + split_part_floats(batch, features, hidden) +
+            (size_t)kColChunks * (hidden > 1 ? hidden : 1) + 64) * sizeof(float) + 1024;
 }
 
 extern "C" int mk_mlp_gradient(const float *d_params, int32_t features, int32_t hidden, const uint32_t *d_vec,
@@ -588,6 +680,9 @@ extern "C" int mk_mlp_gradient(const float *d_params, int32_t features, int32_t 
     float *h1 = (float *)d_workspace, *h2 = h1 + (size_t)batch * H;
     float *dh1 = h2 + (size_t)batch * H, *dh2 = dh1 + (size_t)batch * H;
     float *z = dh2 + (size_t)batch * H, *dz = z + batch;
+    float *part = (float *)d_workspace + ((train_base_floats(batch, F, H) + 63) & ~(size_t)63);
+    const size_t part_floats = split_part_floats(batch, F, H);
+    float *cpart = part + part_floats;
     cudaMemsetAsync(d_loss, 0, sizeof(float), s);
     GemmArgs g;
     // forward
@@ -595,33 +690,35 @@ extern "C" int mk_mlp_gradient(const float *d_params, int32_t features, int32_t 
     g.M = batch; g.N = H; g.K = F;
     g.vec = d_vec; g.pa = d_pa; g.pb = d_pb; g.vwords = F / 64;
     g.B = v.W1; g.ldb = H; g.C = h1; g.ldc = H; g.bias = v.b1; g.relu = 1;
-    gemm<A_PAIR, B_ROW>(g, s);
+    gemm<A_PAIR, B_ROW>(g, s, part, part_floats);
     std::memset(&g, 0, sizeof(g));
     g.M = batch; g.N = H; g.K = H;
     g.A = h1; g.lda = H; g.B = v.W2; g.ldb = H; g.C = h2; g.ldc = H; g.bias = v.b2; g.relu = 1;
-    gemm<A_ROW, B_ROW>(g, s);
+    gemm<A_ROW, B_ROW>(g, s, part, part_floats);
     head_kernel<<<(batch + 7) / 8, 256, 0, s>>>(h2, v.w3, v.b3, d_y, d_w, batch, H, z, dz, d_loss);
-    // backward
-    head_back_kernel<<<(H + 255) / 256, 256, 0, s>>>(h2, v.w3, dz, batch, H, dh2, gv.w3, gv.b3);
+    // backward: dh2, dw3 = sum_p dz[p] h2[p], db3 = sum_p dz[p]
+    head_grad_kernel<<<1024, 256, 0, s>>>(h2, v.w3, dz, batch, H, dh2);
+    colsum(h2, dz, batch, H, gv.w3, cpart, s);
+    colsum(dz, nullptr, batch, 1, gv.b3, cpart, s);
     // dW2 = h1^T dh2 ; db2 = colsum dh2
     std::memset(&g, 0, sizeof(g));
     g.M = H; g.N = H; g.K = batch;
     g.A = h1; g.lda = H; g.B = dh2; g.ldb = H; g.C = gv.W2; g.ldc = H;
-    gemm<A_COL, B_ROW>(g, s);
-    colsum_kernel<<<(H + 255) / 256, 256, 0, s>>>(dh2, batch, H, gv.b2);
+    gemm<A_COL, B_ROW>(g, s, part, part_floats);
+    colsum(dh2, nullptr, batch, H, gv.b2, cpart, s);
     // dh1 = dh2 W2^T, then through the first ReLU
     std::memset(&g, 0, sizeof(g));
     g.M = batch; g.N = H; g.K = H;
     g.A = dh2; g.lda = H; g.B = v.W2; g.ldb = H; g.C = dh1; g.ldc = H;
-    gemm<A_ROW, B_COL>(g, s);
+    gemm<A_ROW, B_COL>(g, s, part, part_floats);
     relu_back_kernel<<<1024, 256, 0, s>>>(dh1, h1, (size_t)batch * H);
     // dW1 = X^T dh1 ; db1 = colsum dh1
     std::memset(&g, 0, sizeof(g));
     g.M = F; g.N = H; g.K = batch;
     g.vec = d_vec; g.pa = d_pa; g.pb = d_pb; g.vwords = F / 64;
     g.B = dh1; g.ldb = H; g.C = gv.W1; g.ldc = H;
-    gemm<A_PAIR_T, B_ROW>(g, s);
-    colsum_kernel<<<(H + 255) / 256, 256, 0, s>>>(dh1, batch, H, gv.b1);
+    gemm<A_PAIR_T, B_ROW>(g, s, part, part_floats);
+    colsum(dh1, nullptr, batch, H, gv.b1, cpart, s);
     return cudaGetLastError() == cudaSuccess ? MK_OK : MK_E_CUDA;
 }
 
