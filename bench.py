@@ -970,7 +970,7 @@ def run_mlp(args):
            "mma_sync_tflops": flops / (res["mma"] / 1e3) / 1e12,
            "speedup_vs_mma_sync": res["mma"] / res["ws"],
            "training_step": {"pairs": TB, "ms": train_ms, "tflops": train_tflops,
-                             "roofline": {"bound": "fp32 (SIMT)", "kernel": "gemm_f32_kernel (+ head, Adam)",
+                             "roofline": {"bound": "fp32 (SIMT)", "kernel": "gemm_pair_kernel, gemm_f32_kernel (+ head, Adam)",
                                           "achieved": train_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
                                           "frac": train_tflops / fp32_peak,
                                           "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FMA) x %.0f MHz"

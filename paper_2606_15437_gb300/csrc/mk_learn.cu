@@ -230,6 +230,38 @@ __device__ __forceinline__ float load_b(const GemmArgs &g, int k, int n) {
     else return g.B[(size_t)n * g.ldb + k];
 }
 
+// A thread's 8 x 8 outputs at (mb, nb): the raw sums into the split-K
+// partials, or C = acc + beta * C + bias, then the ReLU.
+__device__ __forceinline__ void gemm_store(const GemmArgs &g, const float (&acc)[8][8], int mb, int nb) {
+    if (g.part) {
+        float *pz = g.part + (size_t)blockIdx.z * g.M * g.N;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int m = mb + i;
+            if (m >= g.M) continue;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (nb + j < g.N) pz[(size_t)m * g.N + nb + j] = acc[i][j];
+        }
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int m = mb + i;
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int n = nb + j;
+            if (n >= g.N) continue;
+            float v = acc[i][j];
+            if (g.beta != 0.f) v += g.beta * g.C[(size_t)m * g.ldc + n];
+            if (g.bias) v += g.bias[n];
+            if (g.relu) v = v > 0.f ? v : 0.f;
+            g.C[(size_t)m * g.ldc + n] = v;
+        }
+    }
+}
+
 template <int AMODE, int BMODE>
 __global__ void __launch_bounds__(256) gemm_f32_kernel(GemmArgs g) {
     __shared__ float As[GBK][GBM + 4];
@@ -269,33 +301,112 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(GemmArgs g) {
         }
         __syncthreads();
     }
-    if (g.part) {
-        float *pz = g.part + (size_t)blockIdx.z * g.M * g.N;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int m = m0 + tm + i;
-            if (m >= g.M) continue;
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (n0 + tn + j < g.N) pz[(size_t)m * g.N + n0 + tn + j] = acc[i][j];
+    gemm_store(g, acc, m0 + tm, n0 + tn);
+}
+
+// The two GEMMs whose A operand is the pair features x = [a xor b, a and b]
+// (forward x W1: rows = pairs, k = features; dW1 = x^T d1: rows = features,
+// k = pairs), with 32-deep k steps: a truth-vector word holds 32 features,
+// so each word is loaded once per tile row and expanded bit by bit into
+// shared memory (the generic loader fetched two words and two pair indices
+// per element).  B is row-major [K][N].  Features f < F/2 take the xor of
+// word f/32 of the two vectors, the others the and of word f/32 - F/64;
+// F is a multiple of 64, so no 32-feature group straddles the two halves.
+constexpr int PBK = 32;
+
+template <bool TRANS>
+__global__ void __launch_bounds__(256) gemm_pair_kernel(GemmArgs g) {
+    __shared__ __align__(16) float As[PBK][GBM + 4];
+    __shared__ __align__(16) float Bs[PBK][GBN + 4];
+    const int tid = threadIdx.x;
+    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+    const int tm = (tid / 16) * 8, tn = (tid % 16) * 8;
+    const int F = g.vwords * 64, halfF = g.vwords * 32;
+    const bool bvec = (g.ldb & 3) == 0 && ((uintptr_t)g.B & 15) == 0;   // rows of B load as float4
+    // forward: thread t < 128 owns pair m0 + t for the whole K loop
+    int ia = 0, ib = 0;
+    bool prow = false;
+    if constexpr (!TRANS) {
+        if (tid < GBM && m0 + tid < g.M) {
+            ia = g.pa[m0 + tid];
+            ib = g.pb[m0 + tid];
+            prow = true;
         }
-        return;
     }
+    float acc[8][8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int m = m0 + tm + i;
-        if (m >= g.M) continue;
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int n = n0 + tn + j;
-            if (n >= g.N) continue;
-            float v = acc[i][j];
-            if (g.beta != 0.f) v += g.beta * g.C[(size_t)m * g.ldc + n];
-            if (g.bias) v += g.bias[n];
-            if (g.relu) v = v > 0.f ? v : 0.f;
-            g.C[(size_t)m * g.ldc + n] = v;
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    const int kb = g.kchunk ? (int)blockIdx.z * g.kchunk : 0;
+    const int ke = g.kchunk ? min(g.K, kb + g.kchunk) : g.K;
+    for (int k0 = kb; k0 < ke; k0 += PBK) {
+        if constexpr (!TRANS) {
+            // A[pair][feature]: one word of each vector per pair and k step
+            if (tid < GBM) {
+                uint32_t x = 0;
+                if (prow) {
+                    const bool xr = k0 < halfF;
+                    const int w = (xr ? k0 : k0 - halfF) >> 5;
+                    const uint32_t a = g.vec[(size_t)ia * g.vwords + w], b = g.vec[(size_t)ib * g.vwords + w];
+                    x = xr ? (a ^ b) : (a & b);
+                }
+#pragma unroll
+                for (int kk = 0; kk < PBK; ++kk) As[kk][tid] = (k0 + kk < ke) ? (float)((x >> kk) & 1u) : 0.f;
+            }
+        } else {
+            // A[feature][pair]: thread (pair kk, sixteenth j) expands 16 features
+            const int kk = tid >> 3, j = tid & 7;
+            const int p = k0 + kk;
+            const int f0 = m0 + j * 16;
+            uint32_t x = 0;
+            if (p < ke && f0 < F) {
+                const int ja = g.pa[p], jb = g.pb[p];
+                const bool xr = f0 < halfF;
+                const int w = (xr ? f0 : f0 - halfF) >> 5;
+                const uint32_t a = g.vec[(size_t)ja * g.vwords + w], b = g.vec[(size_t)jb * g.vwords + w];
+                x = (xr ? (a ^ b) : (a & b)) >> (f0 & 16);
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) As[kk][j * 16 + i] = (float)((x >> i) & 1u);
         }
+        // B[k][n]: 32 rows of 128 columns, 16 per thread
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = tid + r * 256;               // float4 index in the 32 x 32 float4 tile
+            const int bk = e >> 5, bn = (e & 31) * 4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k0 + bk < ke) {
+                const float *row = g.B + (size_t)(k0 + bk) * g.ldb + n0 + bn;
+                if (bvec && n0 + bn + 3 < g.N) {
+                    v = *reinterpret_cast<const float4 *>(row);
+                } else {
+                    if (n0 + bn < g.N) v.x = row[0];
+                    if (n0 + bn + 1 < g.N) v.y = row[1];
+                    if (n0 + bn + 2 < g.N) v.z = row[2];
+                    if (n0 + bn + 3 < g.N) v.w = row[3];
+                }
+            }
+            *reinterpret_cast<float4 *>(&Bs[bk][bn]) = v;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < PBK; ++kk) {
+            float a[8], b[8];
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][tm]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][tm + 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[kk][tn]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[kk][tn + 4]);
+            a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w; a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+            b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w; b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
     }
+    gemm_store(g, acc, m0 + tm, n0 + tn);
 }
 
 // Split-K epilogue: C = sum_z part[z] (z in order, so the result does not
@@ -590,13 +701,20 @@ void gemm(const GemmArgs &g0, cudaStream_t s, float *part = nullptr, size_t part
         while (S > 1 && (size_t)S * g.M * g.N > part_floats) --S;
     }
     dim3 grid((unsigned)((g.N + GBN - 1) / GBN), (unsigned)((g.M + GBM - 1) / GBM), (unsigned)S);
+    // the pair-feature operand has its own kernel (32-deep k steps)
+    constexpr bool pair = (AM == A_PAIR || AM == A_PAIR_T) && BM == B_ROW;
+    constexpr int step = pair ? PBK : GBK;
+    auto launch = [&](const GemmArgs &a) {
+        if constexpr (pair) gemm_pair_kernel<AM == A_PAIR_T><<<grid, 256, 0, s>>>(a);
+        else gemm_f32_kernel<AM, BM><<<grid, 256, 0, s>>>(a);
+    };
     if (S == 1) {
-        gemm_f32_kernel<AM, BM><<<grid, 256, 0, s>>>(g);
+        launch(g);
         return;
     }
-    g.kchunk = ((g.K + S - 1) / S + GBK - 1) / GBK * GBK;
+    g.kchunk = ((g.K + S - 1) / S + step - 1) / step * step;
     g.part = part;
-    gemm_f32_kernel<AM, BM><<<grid, 256, 0, s>>>(g);
+    launch(g);
     splitk_epilogue_kernel<<<1024, 256, 0, s>>>(part, S, g.M, g.N, g0.C, g0.ldc, g0.bias, g0.relu, g0.beta);
 }
 
