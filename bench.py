@@ -78,6 +78,7 @@ def parse():
                          "formulas of the uneven batch, one persistent launch twice; "
                          "census5:F -- run the K n=5 layer of the first F five-world formulas twice "
                          "(a warm-up and the launch an ncu capture selects with -s 1 -c 1), then exit; "
+                         "train:B -- two MLP training steps on B pairs; "
                          "separation:P -- the same for the first P separation pairs at n=6; separation6:P -- the "
                          "first P pairs that agree through five worlds, at n=6 (the bench's dominant kernel); "
                          "stress:P -- the first P mining candidates on 2^16 12-world relations (two "
@@ -1035,6 +1036,25 @@ def run_profile_case(spec):
                                     net.params[F * H:].data_ptr(), h1.data_ptr(), st.data_ptr(), 0)
         torch.cuda.synchronize()
         print("profile case %s done (status %d)" % (spec, int(st.item())))
+        return
+    elif kind == "train":
+        # `count` pairs of one MLP training step (loss, gradient, Adam), twice
+        from paper_2606_15437_gb300 import mk
+        F, H = 8192, 256
+        rng = np.random.default_rng(7)
+        vec = torch.from_numpy(rng.integers(0, 2 ** 32, size=(10000, F // 64), dtype=np.uint64)
+                               .astype(np.uint32).view(np.int32)).cuda()
+        tpa = torch.from_numpy(rng.integers(0, 10000, size=count).astype(np.int32)).cuda()
+        tpb = torch.from_numpy(rng.integers(0, 10000, size=count).astype(np.int32)).cuda()
+        y = torch.from_numpy((rng.random(count) < 0.3).astype(np.float32)).cuda()
+        net = E.MLP(F, H, seed=3)
+        for _ in range(2):
+            net.gradient(vec, tpa, tpb, y)
+            net.step += 1
+            mk.adam_step_raw(net.params.data_ptr(), net.grad.data_ptr(), net.m.data_ptr(), net.v.data_ptr(), net.n,
+                             1e-3, 0.9, 0.999, 1e-8, net.step, 1.0 / count, 0)
+        torch.cuda.synchronize()
+        print("profile case %s done" % spec)
         return
     elif kind == "stress":
         # the adversarial panels' dominant shape: one-variable and constant
