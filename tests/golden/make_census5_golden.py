@@ -9,7 +9,7 @@ Sec. 2 over explicit relations, the corpus scan of Alg. 1 in Sec. 4); the
 inputs come from the seeded generators of ``workloads``.  Nothing of the CUDA
 path is imported.
 
-Four files:
+Five files:
 
 * ``census5_n1to4.tsv.gz`` -- every formula, every class, n = 1..4;
 * ``census5_n5_subset.tsv`` -- full five-world layers (all 2^25 K frames,
@@ -21,7 +21,9 @@ Four files:
   variable-free formula of the batch (one valuation per frame);
 * ``census5_n5_extra.tsv`` -- the same for a further seeded sample of
   formulas with variables outside the subset: 60 with one variable, 10 with
-  two and 10 with three (the sampled valuations of S = 256).
+  two and 10 with three (the sampled valuations of S = 256);
+* ``census5_n5_s4s5.tsv.gz`` -- every formula on the full five-world S4
+  (6,942 frames) and S5 (52 frames) layers.
 
 Rows: formula index, class, n, cm_count, frames_refuted, witness as
 "frame,valuation,world" (K index; valuation index or sample slot; least
@@ -35,10 +37,12 @@ resumes from its partial file):
     python tests/golden/make_census5_golden.py --part n5
     python tests/golden/make_census5_golden.py --part n5k0
     python tests/golden/make_census5_golden.py --part n5extra
+    python tests/golden/make_census5_golden.py --part n5s4s5 --procs 8
 """
 import argparse
 import gzip
 import hashlib
+import multiprocessing
 import os
 import random
 import re
@@ -151,10 +155,44 @@ def run(texts, units, partial, log_every=200):
     return done
 
 
+def _unit_worker(u):
+    """One (formula, class, n) unit in a worker process (one OpenMP thread)."""
+    p, c, n = u
+    return u, fmt(p, c, n, oracle.census(_TEXTS[p], c, n, samples=_SAMPLES[n]))
+
+
+def _init_worker():
+    global _TEXTS, _SAMPLES
+    _TEXTS = W.census5_formulas(SEED)
+    _SAMPLES = {n: W.sampled_valuations(SEED, n, S) for n in range(1, 6)}
+
+
+def run_pool(units, partial, procs, log_every=500):
+    """``run`` spread over ``procs`` worker processes; rows keyed by unit."""
+    done = {}
+    if os.path.exists(partial):
+        with open(partial) as f:
+            for line in f:
+                p, c, n = line.split("\t")[:3]
+                done[(int(p), c, int(n))] = line.rstrip("\n")
+    todo = [u for u in units if u not in done]
+    t0 = time.time()
+    ctx = multiprocessing.get_context("spawn")
+    with ctx.Pool(procs, initializer=_init_worker) as pool, open(partial, "a") as f:
+        for i, (u, line) in enumerate(pool.imap_unordered(_unit_worker, todo, chunksize=4)):
+            f.write(line + "\n")
+            f.flush()
+            done[u] = line
+            if i % log_every == 0:
+                print("%d/%d units, %.0f s" % (i, len(todo), time.time() - t0), flush=True)
+    return done
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--part", choices=("n1to4", "n5", "n5k0", "n5extra"), required=True)
+    ap.add_argument("--part", choices=("n1to4", "n5", "n5k0", "n5extra", "n5s4s5"), required=True)
     ap.add_argument("--workdir", default=HERE, help="where the resumable partial file lives")
+    ap.add_argument("--procs", type=int, default=1, help="worker processes (n5s4s5)")
     args = ap.parse_args()
     texts = W.census5_formulas(SEED)
     oracle.build()
@@ -186,6 +224,16 @@ def main():
             for p in extra:
                 for c in CLASSES:
                     f.write(rows[(p, c, 5)] + "\n")
+    elif args.part == "n5s4s5":
+        os.environ["OMP_NUM_THREADS"] = "1"
+        units = [(p, c, 5) for p in range(len(texts)) for c in ("S4", "S5")]
+        partial = os.path.join(args.workdir, "census5_n5_s4s5.partial")
+        rows = run_pool(units, partial, args.procs)
+        out = os.path.join(HERE, "census5_n5_s4s5.tsv.gz")
+        with gzip.open(out, "wt") as f:
+            f.write("\n".join(header(texts, "every formula, classes S4/S5, n = 5")) + "\n")
+            for u in units:
+                f.write(rows[u] + "\n")
     elif args.part == "n5k0":
         k0 = [p for p in range(len(texts)) if oracle.nvars(texts[p]) == 0]
         units = [(p, c, 5) for p in k0 for c in CLASSES]
