@@ -17,6 +17,7 @@ collective: the barrier and the max of the timings are the only exchange).
 relations) on bounded samples of the same workload on the host cores.
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -312,6 +313,11 @@ def run_mk(args):
     e2e_ms = e0.elapsed_time(e1)
     h2d = h_progs.numel() + h_samples.numel()
     d2h = sum(h.numel() * 8 for h in h_outs)
+    # checksum of every result of the last step (counts and witness keys of
+    # every formula, class and n): equal across runs, GPUs and tunes
+    digest = hashlib.sha256()
+    for h in h_outs:
+        digest.update(h.numpy().tobytes())
 
     # logic-op ceiling cross-check (own calibration kernel)
     sink = torch.zeros(SMS * 8, dtype=torch.int32, device=dev)
@@ -365,6 +371,7 @@ def run_mk(args):
                         "calibrated_lop3_tops": cal_tops},
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
            "gpu_launches": sum(c["launches"] for c in calls) * args.steps,
+           "results_sha256": digest.hexdigest(), "seeds": {"formulas": SEED, "valuations": SEED},
            "clocks": clk}
     if not args.no_cpu_baseline:
         e, s, desc = oracle_sample(formulas, table[5], args.cpu_seconds)
