@@ -308,24 +308,78 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(GemmArgs g) {
 // (forward x W1: rows = pairs, k = features; dW1 = x^T d1: rows = features,
 // k = pairs), with 32-deep k steps: a truth-vector word holds 32 features,
 // so each word is loaded once per tile row and expanded bit by bit into
-// shared memory (the generic loader fetched two words and two pair indices
-// per element).  B is row-major [K][N].  Features f < F/2 take the xor of
+// shared memory.  B is row-major [K][N].  Features f < F/2 take the xor of
 // word f/32 of the two vectors, the others the and of word f/32 - F/64;
 // F is a multiple of 64, so no 32-feature group straddles the two halves.
+//
+// Both operand tiles are double-buffered.  After the barrier that opens k
+// step t, the CTA starts the B copies of step t+1 (cp.async, 16 bytes each,
+// zero-filled past K) into the buffer step t-1 used, and loads the truth-
+// vector words of step t+1 into registers (the transposed GEMM also the pair
+// indices of step t+2); it then runs step t's FMAs and only afterwards
+// expands those words into the other A buffer.  One barrier per k step
+// separates the buffers, and the global loads run under the arithmetic.
 constexpr int PBK = 32;
+constexpr int PAIR_AS = PBK * (GBM + 4), PAIR_BS = PBK * (GBN + 4);   // floats per buffer
+constexpr size_t kPairSmem = 2 * (size_t)(PAIR_AS + PAIR_BS) * sizeof(float);
+
+__device__ __forceinline__ void pair_cp16(uint32_t dst, const void *src, uint32_t bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void pair_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void pair_cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// B rows [k0, k0 + 32) x columns [n0, n0 + 128) into one buffer: by cp.async
+// when every column exists and rows are 16-byte aligned, else by plain loads.
+__device__ __forceinline__ void pair_load_b(const GemmArgs &g, float *bs, int k0, int ke, int n0, bool basync) {
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int e = tid + r * 256;                   // float4 index in the 32 x 32 float4 tile
+        const int bk = e >> 5, bn = (e & 31) * 4;
+        float *dst = bs + bk * (GBN + 4) + bn;
+        if (basync) {
+            const bool in = k0 + bk < ke;
+            const float *src = in ? g.B + (size_t)(k0 + bk) * g.ldb + n0 + bn : g.B;
+            pair_cp16((uint32_t)__cvta_generic_to_shared(dst), src, in ? 16u : 0u);
+        } else {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k0 + bk < ke) {
+                const float *row = g.B + (size_t)(k0 + bk) * g.ldb + n0 + bn;
+                if (n0 + bn < g.N) v.x = row[0];
+                if (n0 + bn + 1 < g.N) v.y = row[1];
+                if (n0 + bn + 2 < g.N) v.z = row[2];
+                if (n0 + bn + 3 < g.N) v.w = row[3];
+            }
+            *reinterpret_cast<float4 *>(dst) = v;
+        }
+    }
+    if (basync) pair_cp_commit();
+}
 
 template <bool TRANS>
-__global__ void __launch_bounds__(256) gemm_pair_kernel(GemmArgs g) {
-    __shared__ __align__(16) float As[PBK][GBM + 4];
-    __shared__ __align__(16) float Bs[PBK][GBN + 4];
+__global__ void __launch_bounds__(256, 2) gemm_pair_kernel(GemmArgs g) {
+    extern __shared__ __align__(16) float pair_smem[];
+    float *const As = pair_smem;                      // [2][PBK][GBM + 4]
+    float *const Bs = pair_smem + 2 * PAIR_AS;        // [2][PBK][GBN + 4]
     const int tid = threadIdx.x;
     const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
     const int tm = (tid / 16) * 8, tn = (tid % 16) * 8;
     const int F = g.vwords * 64, halfF = g.vwords * 32;
-    const bool bvec = (g.ldb & 3) == 0 && ((uintptr_t)g.B & 15) == 0;   // rows of B load as float4
+    const bool basync = (g.ldb & 3) == 0 && ((uintptr_t)g.B & 15) == 0 && n0 + GBN <= g.N;
+    const int kb = g.kchunk ? (int)blockIdx.z * g.kchunk : 0;
+    const int ke = g.kchunk ? min(g.K, kb + g.kchunk) : g.K;
+    const int nt = ke > kb ? (ke - kb + PBK - 1) / PBK : 0;
+
     // forward: thread t < 128 owns pair m0 + t for the whole K loop
     int ia = 0, ib = 0;
     bool prow = false;
+    // transposed: thread (pair row tk of the step, sixteenth tj of the features)
+    const int tk = tid >> 3, tj = tid & 7;
+    const int f0 = m0 + tj * 16;
+    const bool fcol = f0 < F;
+    const int fw = (f0 < halfF ? f0 : f0 - halfF) >> 5;
+    int nja = 0, njb = 0;                             // pair indices of the next step's row
     if constexpr (!TRANS) {
         if (tid < GBM && m0 + tid < g.M) {
             ia = g.pa[m0 + tid];
@@ -333,79 +387,101 @@ __global__ void __launch_bounds__(256) gemm_pair_kernel(GemmArgs g) {
             prow = true;
         }
     }
+
+    // A words of the step at k0: forward, word k0/32 of this thread's pair;
+    // transposed, word f0/32 of pair (ja, jb) (valid rows only)
+    auto expand = [&](float *as, int k0, uint32_t a, uint32_t b) {
+        if constexpr (!TRANS) {
+            if (tid < GBM) {
+                const uint32_t x = k0 < halfF ? (a ^ b) : (a & b);
+#pragma unroll
+                for (int kk = 0; kk < PBK; ++kk)
+                    as[kk * (GBM + 4) + tid] = (k0 + kk < ke) ? (float)((x >> kk) & 1u) : 0.f;
+            }
+        } else {
+            const uint32_t x = (f0 < halfF ? (a ^ b) : (a & b)) >> (f0 & 16);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) as[tk * (GBM + 4) + tj * 16 + i] = (float)((x >> i) & 1u);
+        }
+    };
+
     float acc[8][8];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-    const int kb = g.kchunk ? (int)blockIdx.z * g.kchunk : 0;
-    const int ke = g.kchunk ? min(g.K, kb + g.kchunk) : g.K;
-    for (int k0 = kb; k0 < ke; k0 += PBK) {
+
+    // prologue: step 0 into buffer 0; the transposed GEMM's indices of step 1
+    if (nt > 0) {
+        pair_load_b(g, Bs, kb, ke, n0, basync);
+        uint32_t a = 0, b = 0;
         if constexpr (!TRANS) {
-            // A[pair][feature]: one word of each vector per pair and k step
-            if (tid < GBM) {
-                uint32_t x = 0;
-                if (prow) {
-                    const bool xr = k0 < halfF;
-                    const int w = (xr ? k0 : k0 - halfF) >> 5;
-                    const uint32_t a = g.vec[(size_t)ia * g.vwords + w], b = g.vec[(size_t)ib * g.vwords + w];
-                    x = xr ? (a ^ b) : (a & b);
-                }
-#pragma unroll
-                for (int kk = 0; kk < PBK; ++kk) As[kk][tid] = (k0 + kk < ke) ? (float)((x >> kk) & 1u) : 0.f;
+            if (prow) {
+                const int w = (kb < halfF ? kb : kb - halfF) >> 5;
+                a = g.vec[(size_t)ia * g.vwords + w];
+                b = g.vec[(size_t)ib * g.vwords + w];
             }
         } else {
-            // A[feature][pair]: thread (pair kk, sixteenth j) expands 16 features
-            const int kk = tid >> 3, j = tid & 7;
-            const int p = k0 + kk;
-            const int f0 = m0 + j * 16;
-            uint32_t x = 0;
-            if (p < ke && f0 < F) {
-                const int ja = g.pa[p], jb = g.pb[p];
-                const bool xr = f0 < halfF;
-                const int w = (xr ? f0 : f0 - halfF) >> 5;
-                const uint32_t a = g.vec[(size_t)ja * g.vwords + w], b = g.vec[(size_t)jb * g.vwords + w];
-                x = (xr ? (a ^ b) : (a & b)) >> (f0 & 16);
+            if (kb + tk < ke && fcol) {
+                const int ja = g.pa[kb + tk], jb = g.pb[kb + tk];
+                a = g.vec[(size_t)ja * g.vwords + fw];
+                b = g.vec[(size_t)jb * g.vwords + fw];
             }
-#pragma unroll
-            for (int i = 0; i < 16; ++i) As[kk][j * 16 + i] = (float)((x >> i) & 1u);
+            if (nt > 1 && kb + PBK + tk < ke && fcol) {
+                nja = g.pa[kb + PBK + tk];
+                njb = g.pb[kb + PBK + tk];
+            }
         }
-        // B[k][n]: 32 rows of 128 columns, 16 per thread
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int e = tid + r * 256;               // float4 index in the 32 x 32 float4 tile
-            const int bk = e >> 5, bn = (e & 31) * 4;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (k0 + bk < ke) {
-                const float *row = g.B + (size_t)(k0 + bk) * g.ldb + n0 + bn;
-                if (bvec && n0 + bn + 3 < g.N) {
-                    v = *reinterpret_cast<const float4 *>(row);
-                } else {
-                    if (n0 + bn < g.N) v.x = row[0];
-                    if (n0 + bn + 1 < g.N) v.y = row[1];
-                    if (n0 + bn + 2 < g.N) v.z = row[2];
-                    if (n0 + bn + 3 < g.N) v.w = row[3];
+        expand(As, kb, a, b);
+    }
+
+    for (int t = 0; t < nt; ++t) {
+        const int k0 = kb + t * PBK;
+        const float *as = As + (t & 1) * PAIR_AS, *bs = Bs + (t & 1) * PAIR_BS;
+        float *as_next = As + ((t + 1) & 1) * PAIR_AS, *bs_next = Bs + ((t + 1) & 1) * PAIR_BS;
+        if (basync) pair_cp_wait_all();
+        __syncthreads();                               // step t's tiles are in; step t-1's reads are done
+        const bool more = t + 1 < nt;
+        const int k1 = k0 + PBK;
+        uint32_t a = 0, b = 0;                         // step t+1's words
+        if (more) {
+            pair_load_b(g, bs_next, k1, ke, n0, basync);
+            if constexpr (!TRANS) {
+                if (prow) {
+                    const int w = (k1 < halfF ? k1 : k1 - halfF) >> 5;
+                    a = g.vec[(size_t)ia * g.vwords + w];
+                    b = g.vec[(size_t)ib * g.vwords + w];
+                }
+            } else {
+                if (k1 + tk < ke && fcol) {
+                    a = g.vec[(size_t)nja * g.vwords + fw];
+                    b = g.vec[(size_t)njb * g.vwords + fw];
+                }
+                if (t + 2 < nt && k1 + PBK + tk < ke && fcol) {
+                    nja = g.pa[k1 + PBK + tk];
+                    njb = g.pb[k1 + PBK + tk];
                 }
             }
-            *reinterpret_cast<float4 *>(&Bs[bk][bn]) = v;
         }
-        __syncthreads();
 #pragma unroll 8
         for (int kk = 0; kk < PBK; ++kk) {
-            float a[8], b[8];
-            const float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][tm]);
-            const float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][tm + 4]);
-            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[kk][tn]);
-            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[kk][tn + 4]);
-            a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w; a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
-            b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w; b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+            float av[8], bv[8];
+            const float4 a0 = *reinterpret_cast<const float4 *>(as + kk * (GBM + 4) + tm);
+            const float4 a1 = *reinterpret_cast<const float4 *>(as + kk * (GBM + 4) + tm + 4);
+            const float4 b0 = *reinterpret_cast<const float4 *>(bs + kk * (GBN + 4) + tn);
+            const float4 b1 = *reinterpret_cast<const float4 *>(bs + kk * (GBN + 4) + tn + 4);
+            av[0] = a0.x; av[1] = a0.y; av[2] = a0.z; av[3] = a0.w;
+            av[4] = a1.x; av[5] = a1.y; av[6] = a1.z; av[7] = a1.w;
+            bv[0] = b0.x; bv[1] = b0.y; bv[2] = b0.z; bv[3] = b0.w;
+            bv[4] = b1.x; bv[5] = b1.y; bv[6] = b1.z; bv[7] = b1.w;
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
         }
-        __syncthreads();
+        if (more) expand(as_next, k1, a, b);
     }
+    if (basync) pair_cp_wait_all();
     gemm_store(g, acc, m0 + tm, n0 + tn);
 }
 
@@ -705,7 +781,10 @@ void gemm(const GemmArgs &g0, cudaStream_t s, float *part = nullptr, size_t part
     constexpr bool pair = (AM == A_PAIR || AM == A_PAIR_T) && BM == B_ROW;
     constexpr int step = pair ? PBK : GBK;
     auto launch = [&](const GemmArgs &a) {
-        if constexpr (pair) gemm_pair_kernel<AM == A_PAIR_T><<<grid, 256, 0, s>>>(a);
+        if constexpr (pair) {
+            ensure_dynamic_smem((const void *)gemm_pair_kernel<AM == A_PAIR_T>, kPairSmem);
+            gemm_pair_kernel<AM == A_PAIR_T><<<grid, 256, kPairSmem, s>>>(a);
+        }
         else gemm_f32_kernel<AM, BM><<<grid, 256, 0, s>>>(a);
     };
     if (S == 1) {
