@@ -4,8 +4,10 @@ The five-world census batch (5,624 formulas, K/T/S4/S5, S = 256) runs exactly
 as bench.py launches it (engine.CENSUS5_CALLS), and every count, refuted-
 frame count and witness key is compared with the values
 tests/golden/make_census5_golden.py wrote from the oracle: all formulas at
-n = 1..4, and full five-world layers of a stratified subset (every variable
-count, the longest and deepest formulas, the three axioms).  The separation
+n = 1..4; full five-world layers of a stratified subset (every variable
+count, the longest and deepest formulas, the three axioms), of every
+variable-free formula and of a further seeded sample with variables; and
+every formula's five-world S4 and S5 layers.  The separation
 workload (1,024 pairs) runs exactly as bench.py searches it
 (engine.SEPARATION_SEARCH), and every first split is compared with the
 oracle's: all of them through five worlds, six-world splits below K index
@@ -184,6 +186,21 @@ def test_census_batch_variable_free_five_world_layers_equal_the_oracle(census5):
     want = G.census_rows(name)
     k0 = [p for p in range(len(texts)) if int(progs[p]["nvars"]) == 0]
     assert sorted({p for p, _, _ in want}) == k0 and len(want) == 4 * len(k0)
+    bad = [(p, c) for (p, c, n), (cm, fr, w) in want.items()
+           if tuple(int(x) for x in res[p, CLS.index(c), n - 1]) != (cm, fr, _key(w))]
+    assert not bad, bad[:5]
+
+
+def test_census_batch_every_formula_on_the_five_world_s4_s5_layers(census5):
+    """Every formula of the batch on the full five-world S4 (6,942 frames) and
+    S5 (52 frames) layers, from the device-built frame lists, against the
+    oracle's stored results."""
+    name = "census5_n5_s4s5.tsv.gz"
+    _need(name)
+    texts, _, _, res = census5
+    assert G.header_values(name)["texts_sha256"] == hashlib.sha256("\n".join(texts).encode()).hexdigest()
+    want = G.census_rows(name)
+    assert len(want) == 2 * len(texts)
     bad = [(p, c) for (p, c, n), (cm, fr, w) in want.items()
            if tuple(int(x) for x in res[p, CLS.index(c), n - 1]) != (cm, fr, _key(w))]
     assert not bad, bad[:5]
