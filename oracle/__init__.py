@@ -21,6 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC_TIER1 = os.path.join(_HERE, "tier1.c")
 _lock = threading.Lock()
 _lib = None
 
@@ -28,14 +29,16 @@ CLASSES = ("K", "T", "S4", "S5", "K4")
 
 
 def build(force=False):
-    """Compile oracle.c into _build/liboracle.so (plain gcc, OpenMP)."""
+    """Compile oracle.c (tier 0) and tier1.c (the mask evaluator) into
+    _build/liboracle.so (plain gcc, OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
+    srcs = [_SRC, _SRC_TIER1]
     if (not force and os.path.exists(_SO)
-            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_SO) >= max(os.path.getmtime(x) for x in srcs)):
         return _SO
     tmp = _SO + ".tmp%d" % os.getpid()
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
-                           "-o", tmp, _SRC])
+                           "-o", tmp] + srcs)
     os.replace(tmp, _SO)
     return _SO
 
@@ -90,6 +93,7 @@ def _load():
             lib.orc_frame_condition.argtypes = [i32, i32, p]
             lib.orc_nvars.argtypes = [cs]
             lib.orc_nodes.argtypes = [cs]
+            lib.orc_census_tier1.argtypes = [cs, i32, i32, u32, p, ctypes.POINTER(_Census)]
             _lib = lib
     return _lib
 
@@ -115,6 +119,22 @@ def census(text, cls, n, samples=None, f_lo=0, f_hi=2 ** 64 - 1):
     rc = lib.orc_census(text.encode(), _cls(cls), n, S, ptr, f_lo, f_hi, ctypes.byref(out))
     if rc:
         raise ValueError("oracle census failed (%d) for %r" % (rc, text))
+    return {"frames": out.frames, "cm_count": out.cm_count,
+            "frames_refuted": out.frames_refuted, "nvals": out.nvals,
+            "witness": (out.wf, out.wv, out.ww) if out.found else None}
+
+
+def census_tier1(text, cls, n, samples=None):
+    """``census`` over all frames of one (class, n <= 5) layer, computed by
+    the tier-1 mask evaluator (tier1.c: 64 frames per machine word) instead of
+    tier 0's per-world recursion; the same dict.  Trusted only where it
+    equals ``census`` (tests/test_tier1_oracle.py)."""
+    lib = _load()
+    keep, S, ptr = _samples(samples)
+    out = _Census()
+    rc = lib.orc_census_tier1(text.encode(), _cls(cls), n, S, ptr, ctypes.byref(out))
+    if rc:
+        raise ValueError("tier-1 census failed (%d) for %r" % (rc, text))
     return {"frames": out.frames, "cm_count": out.cm_count,
             "frames_refuted": out.frames_refuted, "nvals": out.nvals,
             "witness": (out.wf, out.wv, out.ww) if out.found else None}

@@ -285,6 +285,26 @@ typedef struct {
     uint32_t ww;              /* witness world                              */
 } orc_census_out;
 
+/* The parse tree of `text`, for the mask evaluator of tier1.c: node i has
+   kind[i] (0 T, 1 F, 2 variable, 3 not, 4 and, 5 or, 6 implies, 7 iff,
+   8 box, 9 diamond), variable var[i] and children a[i], b[i] (-1: none);
+   the parser numbers children before their parents.  The arrays hold
+   ORC_MAX_NODES entries.  Returns 0, or -1 on a parse error. */
+int orc_parse_tree(const char *text, int *kind, int *var, int *a, int *b, int *nn, int *root, int *nvars) {
+    oform f;
+    if (parse(text, &f)) return -1;
+    for (int i = 0; i < f.nn; i++) {
+        kind[i] = f.nd[i].kind;
+        var[i] = f.nd[i].var;
+        a[i] = f.nd[i].a;
+        b[i] = f.nd[i].b;
+    }
+    *nn = f.nn;
+    *root = f.root;
+    *nvars = f.nvars;
+    return 0;
+}
+
 int orc_nvars(const char *text) {
     oform f;
     if (parse(text, &f)) return -1;

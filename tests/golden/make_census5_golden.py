@@ -9,7 +9,7 @@ Sec. 2 over explicit relations, the corpus scan of Alg. 1 in Sec. 4); the
 inputs come from the seeded generators of ``workloads``.  Nothing of the CUDA
 path is imported.
 
-Five files:
+Six files:
 
 * ``census5_n1to4.tsv.gz`` -- every formula, every class, n = 1..4;
 * ``census5_n5_subset.tsv`` -- full five-world layers (all 2^25 K frames,
@@ -23,7 +23,12 @@ Five files:
   formulas with variables outside the subset: 60 with one variable, 10 with
   two and 10 with three (the sampled valuations of S = 256);
 * ``census5_n5_s4s5.tsv.gz`` -- every formula on the full five-world S4
-  (6,942 frames) and S5 (52 frames) layers.
+  (6,942 frames) and S5 (52 frames) layers;
+* ``census5_n5_tier1.tsv.gz`` -- every formula on the full five-world K
+  (2^25 frames) and T (2^20 frames) layers, computed by the oracle's tier-1
+  mask evaluator (``oracle.census_tier1``, 64 frames per machine word)
+  after it has reproduced every five-world layer the files above hold from
+  tier 0 (the run stops at the first difference).
 
 Rows: formula index, class, n, cm_count, frames_refuted, witness as
 "frame,valuation,world" (K index; valuation index or sample slot; least
@@ -38,6 +43,7 @@ resumes from its partial file):
     python tests/golden/make_census5_golden.py --part n5k0
     python tests/golden/make_census5_golden.py --part n5extra
     python tests/golden/make_census5_golden.py --part n5s4s5 --procs 8
+    python tests/golden/make_census5_golden.py --part n5tier1
 """
 import argparse
 import gzip
@@ -188,9 +194,50 @@ def run_pool(units, partial, procs, log_every=500):
     return done
 
 
+def read_rows(path):
+    """The rows of a stored census file, keyed by (formula, class, n)."""
+    opener = gzip.open if path.endswith(".gz") else open
+    out = {}
+    with opener(path, "rt") as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            p, c, n = line.split("\t")[:3]
+            out[(int(p), c, int(n))] = line.rstrip("\n")
+    return out
+
+
+def run_tier1(texts, check, stored, units, partial, log_every=100):
+    """Tier 1 on every unit of ``check`` (compared with tier 0's stored row;
+    stops at the first difference), then on ``units``; rows keyed by unit,
+    resumable from ``partial``."""
+    done = {}
+    if os.path.exists(partial):
+        with open(partial) as f:
+            for line in f:
+                p, c, n = line.split("\t")[:3]
+                done[(int(p), c, int(n))] = line.rstrip("\n")
+    samples = {n: W.sampled_valuations(SEED, n, S) for n in range(1, 6)}
+    t0 = time.time()
+    todo = [u for u in check if u not in done] + [u for u in units if u not in done and u not in stored]
+    todo = list(dict.fromkeys(todo))
+    with open(partial, "a") as f:
+        for i, (p, c, n) in enumerate(todo):
+            line = fmt(p, c, n, oracle.census_tier1(texts[p], c, n, samples=samples[n]))
+            if (p, c, n) in stored and stored[(p, c, n)] != line:
+                raise SystemExit("tier 1 differs from tier 0 at %r:\n  tier 0 %s\n  tier 1 %s"
+                                 % ((p, c, n), stored[(p, c, n)], line))
+            f.write(line + "\n")
+            f.flush()
+            done[(p, c, n)] = line
+            if i % log_every == 0:
+                print("%d/%d units, %.0f s" % (i, len(todo), time.time() - t0), flush=True)
+    return done
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--part", choices=("n1to4", "n5", "n5k0", "n5extra", "n5s4s5"), required=True)
+    ap.add_argument("--part", choices=("n1to4", "n5", "n5k0", "n5extra", "n5s4s5", "n5tier1"), required=True)
     ap.add_argument("--workdir", default=HERE, help="where the resumable partial file lives")
     ap.add_argument("--procs", type=int, default=1, help="worker processes (n5s4s5)")
     args = ap.parse_args()
@@ -232,6 +279,25 @@ def main():
         out = os.path.join(HERE, "census5_n5_s4s5.tsv.gz")
         with gzip.open(out, "wt") as f:
             f.write("\n".join(header(texts, "every formula, classes S4/S5, n = 5")) + "\n")
+            for u in units:
+                f.write(rows[u] + "\n")
+    elif args.part == "n5tier1":
+        # tier 0's stored five-world layers, which tier 1 must reproduce first
+        stored = {}
+        for name in ("census5_n5_subset.tsv", "census5_n5_k0.tsv", "census5_n5_extra.tsv",
+                     "census5_n5_s4s5.tsv.gz"):
+            path = os.path.join(HERE, name)
+            if os.path.exists(path):
+                stored.update(read_rows(path))
+        check = sorted(stored, key=lambda u: (u[1] == "K", u[0], u[1]))
+        units = [(p, c, 5) for p in range(len(texts)) for c in ("K", "T")]
+        partial = os.path.join(args.workdir, "census5_n5_tier1.partial")
+        rows = run_tier1(texts, check, stored, units, partial)
+        out = os.path.join(HERE, "census5_n5_tier1.tsv.gz")
+        with gzip.open(out, "wt") as f:
+            f.write("\n".join(header(texts, "every formula, classes K/T, n = 5, by the tier-1 mask evaluator "
+                                     "(oracle.census_tier1), which first reproduced all %d five-world "
+                                     "layers stored from tier 0" % len(check))) + "\n")
             for u in units:
                 f.write(rows[u] + "\n")
     elif args.part == "n5k0":
