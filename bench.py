@@ -125,6 +125,24 @@ def oracle_sample(formulas, samples5, budget_s, start_frame=0):
     return evals, secs, desc
 
 
+def tier1_sample(formulas, samples5, budget_s):
+    """Time the oracle's tier-1 mask evaluator (64 frames per machine word,
+    OpenMP; the analogue of a bitmask CPU code) on whole K n=5 layers of the
+    workload's formulas, in order, until the budget is used.  Context beside
+    the tier-0 baseline, not a target."""
+    import oracle
+    oracle.build()
+    evals, t0, count = 0, time.perf_counter(), 0
+    while time.perf_counter() - t0 < budget_s and count < len(formulas):
+        r = oracle.census_tier1(formulas[count], "K", 5, samples=samples5)
+        evals += r["frames"] * r["nvals"]
+        count += 1
+    secs = time.perf_counter() - t0
+    return {"value": evals / secs / 1e9, "unit": UNIT, "cores": oracle.threads(),
+            "kind": "oracle tier 1 (mask evaluator: 64 frames per word, OpenMP)",
+            "sample": "oracle.census_tier1 on the whole K n=5 layer of the first %d workload formulas" % count}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -378,6 +396,7 @@ def run_mk(args):
         import oracle
         out["cpu_baseline"] = {"value": e / s / 1e9, "unit": UNIT, "cores": oracle.threads(),
                                "kind": "oracle", "sample": desc}
+        out["cpu_tier1"] = tier1_sample(formulas, table[5], min(args.cpu_seconds, 15.0))
     if world == 1 and not args.no_secondary:
         out["secondary"] = secondary_results()
     print(json.dumps(out), flush=True)
