@@ -1,7 +1,8 @@
 /*
  * tier1.c -- the oracle's second tier: a mask evaluator for whole census
  * layers, fast enough to compute every five-world layer of a formula batch
- * on the host cores (tier 0, oracle.c, takes hours per formula there).
+ * on the host cores (tier 0, oracle.c, spends about a core-hour on one
+ * five-world K layer with 256 valuations; tier 1 a few core-seconds).
  *
  * TEST INFRASTRUCTURE ONLY, like oracle.c: only tests/ and the scripts that
  * write the stored results under tests/golden/ use it.  It shares no code
