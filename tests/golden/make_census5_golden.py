@@ -126,10 +126,10 @@ def fmt(p, c, n, r):
     return "%d\t%s\t%d\t%d\t%d\t%s" % (p, c, n, r["cm_count"], r["frames_refuted"], w)
 
 
-def header(texts, what):
+def header(texts, what, source="oracle.census only"):
     return ["# Oracle census of the five-world census batch (Sec. 4 Alg. 1; Sec. 6 corpus",
             "# stand-in): %s." % what,
-            "# Written by tests/golden/make_census5_golden.py from oracle.census only.",
+            "# Written by tests/golden/make_census5_golden.py from %s." % source,
             "# inputs: workloads.census5_formulas(seed=%d) (%d formulas), S = %d sampled valuations"
             % (SEED, len(texts), S),
             "# per layer from workloads.sampled_valuations(%d, n, %d)" % (SEED, S),
@@ -297,7 +297,8 @@ def main():
         with gzip.open(out, "wt") as f:
             f.write("\n".join(header(texts, "every formula, classes K/T, n = 5, by the tier-1 mask evaluator "
                                      "(oracle.census_tier1), which first reproduced all %d five-world "
-                                     "layers stored from tier 0" % len(check))) + "\n")
+                                     "layers stored from tier 0" % len(check),
+                                     source="oracle.census_tier1, checked against oracle.census")) + "\n")
             for u in units:
                 f.write(rows[u] + "\n")
     elif args.part == "n5k0":

@@ -98,3 +98,22 @@ def test_separation_file_inputs_and_early_splits_reproduce():
                 first = (n,) + tuple(r["split"][:3])
                 break
         assert first == want[i]["le5"], (i, a, b)
+
+
+def test_tier1_file_inputs_and_sampled_rows_reproduce(census5):
+    """The tier-1 K/T file: input hash, one row per class for every variable
+    count, computed again by the tier-1 evaluator."""
+    name = "census5_n5_tier1.tsv.gz"
+    if not _present([name]):
+        pytest.fail("golden file %s is missing" % name)
+    texts, samples = census5
+    assert G.header_values(name)["texts_sha256"] == hashlib.sha256("\n".join(texts).encode()).hexdigest()
+    want = G.census_rows(name)
+    assert len(want) == 2 * len(texts)
+    rng = random.Random(5)
+    for k in range(4):
+        ps = [p for p in range(len(texts)) if oracle.nvars(texts[p]) == k and len(texts[p]) < 30]
+        p = rng.choice(ps)
+        for c in ("T", "K") if k < 2 else ("T",):
+            got = oracle.census_tier1(texts[p], c, 5, samples=samples[5])
+            assert _row(got) == want[(p, c, 5)], (p, texts[p], c)
