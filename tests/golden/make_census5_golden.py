@@ -9,7 +9,7 @@ Sec. 2 over explicit relations, the corpus scan of Alg. 1 in Sec. 4); the
 inputs come from the seeded generators of ``workloads``.  Nothing of the CUDA
 path is imported.
 
-Six files:
+Five files:
 
 * ``census5_n1to4.tsv.gz`` -- every formula, every class, n = 1..4;
 * ``census5_n5_subset.tsv`` -- full five-world layers (all 2^25 K frames,
@@ -19,9 +19,6 @@ Six files:
   the three axioms;
 * ``census5_n5_k0.tsv`` -- the same full five-world layers for every
   variable-free formula of the batch (one valuation per frame);
-* ``census5_n5_extra.tsv`` -- the same for a further seeded sample of
-  formulas with variables outside the subset: 60 with one variable, 10 with
-  two and 10 with three (the sampled valuations of S = 256);
 * ``census5_n5_s4s5.tsv.gz`` -- every formula on the full five-world S4
   (6,942 frames) and S5 (52 frames) layers;
 * ``census5_n5_tier1.tsv.gz`` -- every formula on the full five-world K
@@ -41,7 +38,6 @@ resumes from its partial file):
     python tests/golden/make_census5_golden.py --part n1to4
     python tests/golden/make_census5_golden.py --part n5
     python tests/golden/make_census5_golden.py --part n5k0
-    python tests/golden/make_census5_golden.py --part n5extra
     python tests/golden/make_census5_golden.py --part n5s4s5 --procs 8
     python tests/golden/make_census5_golden.py --part n5tier1
 """
@@ -237,7 +233,7 @@ def run_tier1(texts, check, stored, units, partial, log_every=100):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--part", choices=("n1to4", "n5", "n5k0", "n5extra", "n5s4s5", "n5tier1"), required=True)
+    ap.add_argument("--part", choices=("n1to4", "n5", "n5k0", "n5s4s5", "n5tier1"), required=True)
     ap.add_argument("--workdir", default=HERE, help="where the resumable partial file lives")
     ap.add_argument("--procs", type=int, default=1, help="worker processes (n5s4s5)")
     args = ap.parse_args()
@@ -252,25 +248,6 @@ def main():
             f.write("\n".join(header(texts, "every formula, classes K/T/S4/S5, n = 1..4")) + "\n")
             for u in units:
                 f.write(rows[u] + "\n")
-    elif args.part == "n5extra":
-        subset = set(n5_subset(texts))
-        rng = random.Random(11)
-        extra = []
-        for k, count in ((1, 60), (2, 10), (3, 10)):
-            idx = [p for p in range(len(texts)) if oracle.nvars(texts[p]) == k and p not in subset]
-            extra += rng.sample(idx, count)
-        extra.sort()
-        units = [(p, c, 5) for p in extra for c in ("S5", "S4", "T", "K")]
-        units.sort(key=lambda u: (u[1] == "K", oracle.nvars(texts[u[0]]), W.nodes(texts[u[0]])))
-        partial = os.path.join(args.workdir, "census5_n5_extra.partial")
-        rows = run(texts, units, partial, log_every=10)
-        out = os.path.join(HERE, "census5_n5_extra.tsv")
-        with open(out, "w") as f:
-            f.write("\n".join(header(texts, "full n = 5 layers of a further seeded sample of %d formulas with "
-                                     "variables (60 / 10 / 10 with k = 1 / 2 / 3)" % len(extra))) + "\n")
-            for p in extra:
-                for c in CLASSES:
-                    f.write(rows[(p, c, 5)] + "\n")
     elif args.part == "n5s4s5":
         os.environ["OMP_NUM_THREADS"] = "1"
         units = [(p, c, 5) for p in range(len(texts)) for c in ("S4", "S5")]
@@ -284,8 +261,7 @@ def main():
     elif args.part == "n5tier1":
         # tier 0's stored five-world layers, which tier 1 must reproduce first
         stored = {}
-        for name in ("census5_n5_subset.tsv", "census5_n5_k0.tsv", "census5_n5_extra.tsv",
-                     "census5_n5_s4s5.tsv.gz"):
+        for name in ("census5_n5_subset.tsv", "census5_n5_k0.tsv", "census5_n5_s4s5.tsv.gz"):
             path = os.path.join(HERE, name)
             if os.path.exists(path):
                 stored.update(read_rows(path))

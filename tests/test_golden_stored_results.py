@@ -21,7 +21,7 @@ from paper_2606_15437_gb300 import workloads as W
 
 
 CENSUS_FILES = ("census5_n1to4.tsv.gz", "census5_n5_subset.tsv", "census5_n5_k0.tsv",
-                "census5_n5_extra.tsv", "census5_n5_s4s5.tsv.gz")
+                "census5_n5_s4s5.tsv.gz")
 
 
 @pytest.fixture(scope="module", autouse=True)

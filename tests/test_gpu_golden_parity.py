@@ -5,9 +5,8 @@ as bench.py launches it (engine.CENSUS5_CALLS), and every count, refuted-
 frame count and witness key is compared with the values
 tests/golden/make_census5_golden.py wrote from the oracle: all formulas at
 n = 1..4; full five-world layers of a stratified subset (every variable
-count, the longest and deepest formulas, the three axioms), of every
-variable-free formula and of a further seeded sample with variables;
-every formula's five-world S4 and S5 layers; and every formula's five-world
+count, the longest and deepest formulas, the three axioms) and of every
+variable-free formula; every formula's five-world S4 and S5 layers; and every formula's five-world
 K and T layers as the oracle's tier-1 mask evaluator computed them (after
 it had reproduced every five-world layer stored from tier 0).  The separation
 workload (1,024 pairs) runs exactly as bench.py searches it
