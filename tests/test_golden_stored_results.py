@@ -117,3 +117,20 @@ def test_tier1_file_inputs_and_sampled_rows_reproduce(census5):
         for c in ("T", "K") if k < 2 else ("T",):
             got = oracle.census_tier1(texts[p], c, 5, samples=samples[5])
             assert _row(got) == want[(p, c, 5)], (p, texts[p], c)
+
+
+def test_uneven_small_file_inputs_and_sampled_rows_reproduce():
+    """The uneven batch's one-to-three-world file: input hash, every such
+    layer of every job, and a seeded sample computed again by tier 0."""
+    name = "uneven_n1to3.tsv.gz"
+    if not _present([name]):
+        pytest.fail("golden file %s is missing" % name)
+    items = W.uneven_formulas(3)
+    sha = hashlib.sha256("\n".join("%s\t%s\t%d" % it for it in items).encode()).hexdigest()
+    assert G.header_values(name)["items_sha256"] == sha
+    want = G.census_rows(name)
+    assert set(want) == {(j, items[j][1], n) for j in range(len(items)) for n in (1, 2, 3)}
+    samples = {n: W.sampled_valuations(3, n, 64) for n in (1, 2, 3)}
+    for j, c, n in random.Random(10).sample(sorted(want), 40):
+        got = oracle.census(items[j][0], c, n, samples=samples[n])
+        assert _row(got) == want[(j, c, n)], (j, items[j], n)

@@ -14,6 +14,9 @@ workload (1,024 pairs) runs exactly as bench.py searches it
 oracle's: all of them through five worlds, six-world splits below K index
 2^27, and the first sampled 7- and 8-world splits below sample 2^21 for the
 pairs the oracle finds no earlier split for.  Every split is certified.
+The uneven batch (20,000 jobs) runs in one persistent launch, and its layers
+of four and five worlds are compared with the stored results: 440 of them
+from tier 0, all of them from tier 1.
 """
 import hashlib
 import os
@@ -220,4 +223,24 @@ def test_census_batch_every_formula_on_the_five_world_k_t_layers(census5):
     assert len(want) == 2 * len(texts) and {c for _, c, _ in want} == {"K", "T"}
     bad = [(p, c) for (p, c, n), (cm, fr, w) in want.items()
            if tuple(int(x) for x in res[p, CLS.index(c), n - 1]) != (cm, fr, _key(w))]
+    assert not bad, bad[:5]
+
+
+def test_uneven_batch_every_small_layer_equals_the_oracle():
+    """Every layer of one to three worlds of every job of the uneven batch,
+    from one persistent launch, against tier 0's stored results."""
+    from paper_2606_15437_gb300 import engine as E
+    name = "uneven_n1to3.tsv.gz"
+    _need(name)
+    items = W.uneven_formulas(3)
+    sha = hashlib.sha256("\n".join("%s\t%s\t%d" % it for it in items).encode()).hexdigest()
+    assert G.header_values(name)["items_sha256"] == sha
+    t = E.UNEVEN_TUNE
+    job = E.UnevenJob(items, samples=64, seed=3, tiles=tuple(t["tiles"]), tune={"units": t["units"], "block": t["block"]})
+    job.launch()
+    res = job.results().copy()
+    want = G.census_rows(name)
+    assert len(want) == 3 * len(items)
+    bad = [(j, c, n) for (j, c, n), (cm, fr, w) in want.items()
+           if items[j][1] != c or tuple(int(x) for x in res[j, n - 1]) != (cm, fr, _key(w))]
     assert not bad, bad[:5]
