@@ -1,11 +1,10 @@
-"""Writes the oracle's census results for a subset of the uneven batch.
+"""Writes the oracle's census results for the uneven batch.
 
 The uneven batch (``workloads.uneven_formulas(3)``: 20,000 formulas of length
 3-64 and modal depth 1-8, each with its own class and n_max in {3, 4, 5},
 S = 64 sampled valuations per layer from seed 3) is the persistent,
-graph-launched configuration; its layers up to three worlds are checked
-against the oracle at test time.  This script stores the larger layers for
-a seeded subset of jobs:
+graph-launched configuration.  Without options this script stores tier 0's
+larger layers for a seeded subset of jobs (``uneven_subset.tsv``):
 
 * 400 jobs with n_max >= 4: their class's full four-world layer;
 * 40 jobs with n_max = 5: their class's full five-world layer.
