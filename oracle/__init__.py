@@ -94,6 +94,7 @@ def _load():
             lib.orc_nvars.argtypes = [cs]
             lib.orc_nodes.argtypes = [cs]
             lib.orc_census_tier1.argtypes = [cs, i32, i32, u32, p, ctypes.POINTER(_Census)]
+            lib.orc_pair_tier1.argtypes = [cs, cs, i32, u32, p, u64, u64, ctypes.POINTER(_Pair)]
             _lib = lib
     return _lib
 
@@ -138,6 +139,19 @@ def census_tier1(text, cls, n, samples=None):
     return {"frames": out.frames, "cm_count": out.cm_count,
             "frames_refuted": out.frames_refuted, "nvals": out.nvals,
             "witness": (out.wf, out.wv, out.ww) if out.found else None}
+
+
+def pair_tier1(phi, psi, n, samples=None, f_lo=0, f_hi=2 ** 64 - 1):
+    """``pair_layer`` computed by the tier-1 mask evaluator (tier1.c, 64
+    frames per machine word; n <= 6): the same dict.  Trusted only where it
+    equals ``pair_layer`` (tests/test_tier1_oracle.py)."""
+    lib = _load()
+    keep, S, ptr = _samples(samples)
+    out = _Pair()
+    rc = lib.orc_pair_tier1(phi.encode(), psi.encode(), n, S, ptr, f_lo, f_hi, ctypes.byref(out))
+    if rc:
+        raise ValueError("tier-1 pair scan failed (%d) for %r / %r" % (rc, phi, psi))
+    return _pair_dict(out)
 
 
 def _pair_dict(out):

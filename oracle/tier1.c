@@ -42,7 +42,7 @@
 #include <omp.h>
 
 #define T1_MAX_NODES 256   /* oracle.c's ORC_MAX_NODES */
-#define T1_MAX_N 5
+#define T1_MAX_N 6          /* worlds held by the evaluator (the census takes n <= 5) */
 
 int orc_parse_tree(const char *text, int *kind, int *var, int *a, int *b, int *nn, int *root, int *nvars);
 
@@ -170,7 +170,7 @@ int orc_census_tier1(const char *text, int cls, int n, uint32_t S, const uint32_
     static t1_tree zero;
     t1_tree t = zero;
     memset(out, 0, sizeof(*out));
-    if (n < 1 || n > T1_MAX_N || cls < 0 || cls > 4) return -2;
+    if (n < 1 || n > 5 || cls < 0 || cls > 4) return -2;
     if (orc_parse_tree(text, t.kind, t.var, t.a, t.b, &t.nn, &t.root, &t.nvars)) return -1;
     for (int i = 0; i < t.nn; i++)
         if (t.a[i] >= i || t.b[i] >= i) return -1;      /* children first, as the parser numbers them */
@@ -251,6 +251,126 @@ int orc_census_tier1(const char *text, int cls, int n, uint32_t S, const uint32_
         out->wf = best >> 24;
         out->wv = (uint32_t)((best >> 3) & 0x1FFFFFu);
         out->ww = (uint32_t)(best & 7u);
+    }
+    return 0;
+}
+
+/* the layout of oracle.c's orc_pair_out */
+typedef struct {
+    int32_t found, nvals;
+    uint64_t f;
+    uint32_t v, w;
+    int32_t phi_val, psi_val;
+    uint64_t frames_disagree;
+} t1_pair_out;
+
+static int load_tree(const char *text, t1_tree *t) {
+    if (orc_parse_tree(text, t->kind, t->var, t->a, t->b, &t->nn, &t->root, &t->nvars)) return -1;
+    for (int i = 0; i < t->nn; i++)
+        if (t->a[i] >= i || t->b[i] >= i) return -1;
+    return 0;
+}
+
+/* Separation of phi and psi over the K frames on n <= 6 worlds with K index
+   in [f_lo, f_hi): the least (frame, valuation, world) at which the two take
+   different truth values, and the number of frames with any difference --
+   the outputs of oracle.c's orc_pair_layer (Def. 2, Prop. 4).  Returns 0, -1
+   on a parse error, -2 on bad arguments, -3 if sampled valuations are needed
+   and samp is NULL. */
+int orc_pair_tier1(const char *phi, const char *psi, int n, uint32_t S, const uint32_t *samp,
+                   uint64_t f_lo, uint64_t f_hi, t1_pair_out *out) {
+    static t1_tree zero;
+    t1_tree ta = zero, tb = zero;
+    memset(out, 0, sizeof(*out));
+    if (n < 1 || n > T1_MAX_N) return -2;
+    if (load_tree(phi, &ta) || load_tree(psi, &tb)) return -1;
+    const int k = ta.nvars > tb.nvars ? ta.nvars : tb.nvars;
+    const int exh = exhaustive(k, n, S);
+    if (!exh && samp == NULL) return -3;
+    const uint64_t nval = exh ? (uint64_t)1 << (k * n) : S;
+    const uint32_t vmask = (k * n >= 32) ? 0xFFFFFFFFu : (uint32_t)(((uint64_t)1 << (k * n)) - 1);
+    const uint64_t nframes = (uint64_t)1 << (n * n);
+    if (f_hi > nframes) f_hi = nframes;
+    out->nvals = (int32_t)nval;
+    if (f_lo >= f_hi) return 0;
+    const uint64_t b0 = f_lo / (64 * T1_W), b1 = (f_hi + 64 * T1_W - 1) / (64 * T1_W);
+    uint64_t P[6];
+    for (int e = 0; e < 6; e++) P[e] = lane_pattern(e);
+
+    uint64_t dis = 0, best = UINT64_MAX;
+    int best_a = 0;
+#pragma omp parallel
+    {
+        uint64_t TA[T1_MAX_NODES][T1_MAX_N][T1_W], TB[T1_MAX_NODES][T1_MAX_N][T1_W];
+        uint64_t E[T1_MAX_N * T1_MAX_N][T1_W];
+        uint64_t lbest = UINT64_MAX;
+        int lbest_a = 0;
+#pragma omp for schedule(dynamic, 16) reduction(+ : dis)
+        for (int64_t bi = (int64_t)b0; bi < (int64_t)b1; bi++) {
+            edge_words((uint64_t)bi, n, P, E);
+            uint64_t in[T1_W], any[T1_W], best_j[T1_W], best_w[T1_W];
+            int best_lane[T1_W], best_val[T1_W];
+            for (int q = 0; q < T1_W; q++) {
+                /* lanes of word bi*T1_W + q whose frames lie in [f_lo, f_hi) */
+                const uint64_t base = ((uint64_t)bi * T1_W + (uint64_t)q) * 64;
+                uint64_t m = ~(uint64_t)0;
+                if (base + 64 <= f_lo || base >= f_hi) m = 0;
+                else {
+                    if (f_lo > base) m &= ~(uint64_t)0 << (f_lo - base);
+                    if (f_hi < base + 64) m &= ~(~(uint64_t)0 << (f_hi - base));
+                }
+                in[q] = m;
+                any[q] = 0;
+                best_lane[q] = 64;
+                best_j[q] = best_w[q] = 0;
+                best_val[q] = 0;
+            }
+            for (uint64_t j = 0; j < nval; j++) {
+                const uint64_t x = exh ? j : (samp[j] & vmask);
+                eval_tree(&ta, n, (const uint64_t (*)[T1_W])E, x, TA);
+                eval_tree(&tb, n, (const uint64_t (*)[T1_W])E, x, TB);
+                for (int q = 0; q < T1_W; q++) {
+                    uint64_t d = 0;
+                    for (int w = 0; w < n; w++) d |= TA[ta.root][w][q] ^ TB[tb.root][w][q];
+                    d &= in[q];
+                    if (!d) continue;
+                    const uint64_t fresh = d & ~any[q];
+                    if (fresh && __builtin_ctzll(fresh) < best_lane[q]) {
+                        const int L = __builtin_ctzll(fresh);
+                        best_lane[q] = L;
+                        best_j[q] = j;
+                        for (int w = 0; w < n; w++)
+                            if (((TA[ta.root][w][q] ^ TB[tb.root][w][q]) >> L) & 1u) {
+                                best_w[q] = (uint64_t)w;
+                                best_val[q] = (int)((TA[ta.root][w][q] >> L) & 1u);
+                                break;
+                            }
+                    }
+                    any[q] |= d;
+                }
+            }
+            for (int q = 0; q < T1_W; q++) {
+                dis += (uint64_t)__builtin_popcountll(any[q]);
+                if (any[q]) {
+                    const uint64_t frame = ((uint64_t)bi * T1_W + (uint64_t)q) * 64 + (uint64_t)best_lane[q];
+                    const uint64_t key = (frame << 24) | (best_j[q] << 3) | best_w[q];
+                    if (key < lbest) { lbest = key; lbest_a = best_val[q]; }
+                }
+            }
+        }
+#pragma omp critical
+        {
+            if (lbest < best) { best = lbest; best_a = lbest_a; }
+        }
+    }
+    out->frames_disagree = dis;
+    if (best != UINT64_MAX) {
+        out->found = 1;
+        out->f = best >> 24;
+        out->v = (uint32_t)((best >> 3) & 0x1FFFFFu);
+        out->w = (uint32_t)(best & 7u);
+        out->phi_val = best_a;
+        out->psi_val = !best_a;
     }
     return 0;
 }

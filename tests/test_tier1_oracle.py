@@ -85,3 +85,35 @@ def test_tier1_reproduces_stored_five_world_layers(batch):
         want = subset.get((p, c, n)) or k0[(p, c, n)]
         r = oracle.census_tier1(texts[p], c, n, samples=samples[n])
         assert (r["cm_count"], r["frames_refuted"], r["witness"]) == want, (p, texts[p], c)
+
+
+def test_tier1_pair_scan_equals_tier0():
+    """oracle.pair_tier1 (the separation of Def. 2 / Prop. 4 by the mask
+    evaluator) against tier 0's pair_layer: workload pairs through four worlds
+    and on a ragged five-world window, and pairs with variables (exhaustive
+    and sampled valuations)."""
+    pairs = W.separation_pairs(4)
+    rng = random.Random(21)
+    for i in rng.sample(range(len(pairs)), 16) + [0, 1, 32]:
+        a, b = pairs[i]
+        for n in range(1, 5):
+            assert oracle.pair_tier1(a, b, n) == oracle.pair_layer(a, b, n), (i, n)
+        lo, hi = 2000001, 2000001 + 30013
+        assert oracle.pair_tier1(a, b, 5, f_lo=lo, f_hi=hi) == oracle.pair_layer(a, b, 5, f_lo=lo, f_hi=hi), i
+    for a, b in (("[]p -> p", "<>p | ~p"), ("[](p -> q)", "[]p -> []q"), ("<>(p & q)", "<>p & <>q")):
+        for n in range(1, 4):
+            samples = W.sampled_valuations(9, n, 64)
+            assert oracle.pair_tier1(a, b, n) == oracle.pair_layer(a, b, n), (a, b, n)
+            assert oracle.pair_tier1(a, b, n, samples=samples) == oracle.pair_layer(a, b, n, samples=samples)
+
+
+def test_tier1_pair_scan_finds_the_six_world_alpha_split():
+    """alpha_2 / alpha_3 agree on every frame of at most five worlds and first
+    split at six worlds on K index 17,335,328, world 2 (Prop. 5; tier 0 and
+    the pure-Python path give the same): tier 1 finds it scanning the first
+    2^27 six-world frames."""
+    a, b = "[]<>[]<>T", "[]<>[]<>[]<>T"
+    for n in range(1, 6):
+        assert oracle.pair_tier1(a, b, n)["split"] is None
+    r = oracle.pair_tier1(a, b, 6, f_lo=0, f_hi=1 << 27)
+    assert r["split"] == (17335328, 0, 2, 1, 0)
