@@ -25,14 +25,26 @@ What is pinned, per pair:
 Columns hold "n,frame,valuation,world" (le5) or "frame,valuation,world",
 "-" for none and "." for not scanned.
 
-Run from the repository root (about an hour of CPU; resumes from its partial
-file):
+With ``--context`` it writes ``separation_context_pairs.tsv``: for every pair
+that the file above leaves unsplit and whose two formulas are alternating
+context words (only []<> or <>[] steps before T or F: the alpha family and its
+variants) that stay different after []T -> T and <>F -> F (laws that hold
+on every frame, so pairs equal after them never split), the first
+split over ALL 2^36 six-world frames, by the oracle's tier-1 mask evaluator
+(``oracle.pair_tier1``, which first reproduces every six-world split of the
+file above), and the first split among sampled relations [0, 10^8) of 7 and
+8 worlds (the search's full sampled range), by tier 0.
+
+Run from the repository root (about an hour of CPU, then half an hour for
+--context; the first resumes from its partial file):
 
     python tests/golden/make_separation_golden.py
+    python tests/golden/make_separation_golden.py --context
 """
 import argparse
 import hashlib
 import os
+import re
 import sys
 import time
 
@@ -101,12 +113,95 @@ def row(i, a, b):
     return "%d\t-\t-\t%s\t%s" % (i, fmt(s7), fmt(s8))
 
 
+CONTEXT_OUT = os.path.join(HERE, "separation_context_pairs.tsv")
+SAMPLED_FULL = 100_000_000
+ALTERNATING = re.compile(r"((\[\]<>)+|(<>\[\])+)(<>|\[\])?[TF]")
+
+
+def fold(text):
+    """The text with []T -> T and <>F -> F applied until nothing changes
+    (both hold on every frame)."""
+    prev = None
+    while prev != text:
+        prev, text = text, text.replace("[]T", "T").replace("<>F", "F")
+    return text
+
+
+def stored_rows():
+    rows = {}
+    with open(OUT) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            cols = line.rstrip("\n").split("\t")
+            rows[int(cols[0])] = cols[1:]
+    return rows
+
+
+def first_sampled_full(a, b, n):
+    """First split among sampled relations [0, 10^8), in chunks of 2^22."""
+    lo = 0
+    while lo < SAMPLED_FULL:
+        hi = min(lo + (1 << 22), SAMPLED_FULL)
+        r = oracle.pair_sampled(a, b, n, SEED, lo, hi)
+        if r["split"] is not None:
+            return r["split"][:3]
+        lo = hi
+    return None
+
+
+def main_context(pairs):
+    rows = stored_rows()
+    # tier 1 must first reproduce every six-world split tier 0 stored
+    for i, cols in sorted(rows.items()):
+        if cols[1] not in (".", "-"):
+            want = tuple(int(x) for x in cols[1].split(","))
+            a, b = pairs[i]
+            got = oracle.pair_tier1(a, b, 6, f_lo=0, f_hi=want[0] + 1)["split"]
+            if got is None or tuple(got[:3]) != want:
+                raise SystemExit("tier 1 differs from tier 0 on pair %d: %r vs %r" % (i, got, want))
+    pick = [i for i, cols in sorted(rows.items())
+            if cols[0] == "-" and cols[1] == "-" and cols[2] == "-" and cols[3] == "-"
+            and all(ALTERNATING.fullmatch(x) for x in pairs[i])
+            and fold(pairs[i][0]) != fold(pairs[i][1])]
+    t0 = time.time()
+    out = []
+    for i in pick:
+        a, b = pairs[i]
+        r6 = oracle.pair_tier1(a, b, 6)
+        s6 = None if r6["split"] is None else r6["split"][:3]
+        s7 = first_sampled_full(a, b, 7) if s6 is None else "."
+        s8 = first_sampled_full(a, b, 8) if s6 is None and s7 is None else "."
+        out.append("%d\t%s\t%s\t%s\t%d" % (i, fmt(s6), s7 if s7 == "." else fmt(s7),
+                                           s8 if s8 == "." else fmt(s8), r6["frames_disagree"]))
+        print("%s %.0f s" % (out[-1], time.time() - t0), flush=True)
+    with open(CONTEXT_OUT, "w") as f:
+        f.write("# Oracle separation of the workload's unsplit alternating context pairs (Sec. 7;\n"
+                "# Def. 2, Prop. 4): pairs that separation_first_splits.tsv leaves unsplit and whose\n"
+                "# two formulas are alternating context words.  n6: first split over all 2^36 six-world\n"
+                "# frames by the tier-1 mask evaluator (oracle.pair_tier1, which first reproduced every\n"
+                "# six-world split of separation_first_splits.tsv); n7, n8: first split among sampled\n"
+                "# relations [0, 10^8) by tier 0 (oracle.pair_sampled, seed %d).\n"
+                "# Written by tests/golden/make_separation_golden.py --context from oracle only.\n" % SEED)
+        f.write("# pairs_sha256\t%s\n" % pairs_sha(pairs))
+        f.write("# sampled_range\t%d\n" % SAMPLED_FULL)
+        f.write("# columns: pair\tn6(frame,val,world)\tn7(sample,val,world)\tn8(sample,val,world)"
+                "\tn6_frames_disagree; '-' none, '.' not scanned\n")
+        for line in out:
+            f.write(line + "\n")
+    print("wrote", CONTEXT_OUT)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workdir", default=HERE, help="where the resumable partial file lives")
+    ap.add_argument("--context", action="store_true", help="full scans of the unsplit context pairs")
     args = ap.parse_args()
     pairs = W.separation_pairs(SEED)
     oracle.build()
+    if args.context:
+        main_context(pairs)
+        return
     partial = os.path.join(args.workdir, "separation_first_splits.partial")
     done = {}
     if os.path.exists(partial):

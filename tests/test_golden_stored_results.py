@@ -134,3 +134,39 @@ def test_uneven_small_file_inputs_and_sampled_rows_reproduce():
     for j, c, n in random.Random(10).sample(sorted(want), 40):
         got = oracle.census(items[j][0], c, n, samples=samples[n])
         assert _row(got) == want[(j, c, n)], (j, items[j], n)
+
+
+def test_uneven_tier1_file_inputs_and_sampled_rows_reproduce():
+    """The uneven batch's tier-1 file: input hash, one layer per job with
+    n_max >= 4, and a seeded sample of its cheaper rows computed again."""
+    name = "uneven_tier1.tsv.gz"
+    if not _present([name]):
+        pytest.fail("golden file %s is missing" % name)
+    items = W.uneven_formulas(3)
+    sha = hashlib.sha256("\n".join("%s\t%s\t%d" % it for it in items).encode()).hexdigest()
+    assert G.header_values(name)["items_sha256"] == sha
+    want = G.census_rows(name)
+    assert set(want) == {(j, items[j][1], n) for j in range(len(items)) for n in range(4, items[j][2] + 1)}
+    samples = {n: W.sampled_valuations(3, n, 64) for n in (4, 5)}
+    cheap = sorted(u for u in want if u[2] == 4 or u[1] != "K")
+    for j, c, n in random.Random(9).sample(cheap, 8):
+        got = oracle.census_tier1(items[j][0], c, n, samples=samples[n])
+        assert _row(got) == want[(j, c, n)], (j, items[j], n)
+
+
+def test_separation_context_file_inputs_and_a_window_reproduce():
+    """The context-pair file: input hash, and no six-world split in the
+    first 2^24 frames of each listed pair unless the file has one there."""
+    name = "separation_context_pairs.tsv"
+    if not _present([name]):
+        pytest.fail("golden file %s is missing" % name)
+    pairs = W.separation_pairs(4)
+    sha = hashlib.sha256("\n".join(a + "\t" + b for a, b in pairs).encode()).hexdigest()
+    assert G.header_values(name)["pairs_sha256"] == sha
+    for r in G.rows(name):
+        a, b = pairs[int(r[0])]
+        got = oracle.pair_tier1(a, b, 6, f_lo=0, f_hi=1 << 24)["split"]
+        if r[1] == "-" or int(r[1].split(",")[0]) >= 1 << 24:
+            assert got is None, r
+        else:
+            assert ",".join(str(x) for x in got[:3]) == r[1], r

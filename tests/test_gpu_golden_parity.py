@@ -244,3 +244,58 @@ def test_uneven_batch_every_small_layer_equals_the_oracle():
     bad = [(j, c, n) for (j, c, n), (cm, fr, w) in want.items()
            if items[j][1] != c or tuple(int(x) for x in res[j, n - 1]) != (cm, fr, _key(w))]
     assert not bad, bad[:5]
+
+
+def test_uneven_batch_every_four_and_five_world_layer_equals_the_oracle():
+    """Every four- and five-world layer of every job of the uneven batch
+    (n = 4 .. n_max, the job's own class), from one persistent launch, against
+    the stored results of the oracle's tier-1 mask evaluator, which first
+    reproduced the layers stored from tier 0 (uneven_subset.tsv)."""
+    from paper_2606_15437_gb300 import engine as E
+    name = "uneven_tier1.tsv.gz"
+    _need(name)
+    items = W.uneven_formulas(3)
+    sha = hashlib.sha256("\n".join("%s\t%s\t%d" % it for it in items).encode()).hexdigest()
+    assert G.header_values(name)["items_sha256"] == sha
+    t = E.UNEVEN_TUNE
+    job = E.UnevenJob(items, samples=64, seed=3, tiles=tuple(t["tiles"]), tune={"units": t["units"], "block": t["block"]})
+    job.launch()
+    res = job.results().copy()
+    want = G.census_rows(name)
+    assert len(want) == sum(max(0, m - 3) for _, _, m in items)
+    bad = [(j, c, n) for (j, c, n), (cm, fr, w) in want.items()
+           if items[j][1] != c or tuple(int(x) for x in res[j, n - 1]) != (cm, fr, _key(w))]
+    assert not bad, bad[:5]
+
+
+def test_separation_context_pairs_full_ranges_equal_the_oracle():
+    """The workload's unsplit alternating context pairs (the alpha family and
+    its variants that no frame-independent law makes equal), searched exactly
+    as the bench searches them, against the oracle over the search's whole
+    range: every six-world frame (tier 1) and sampled relations [0, 10^8) of
+    seven and eight worlds (tier 0)."""
+    from paper_2606_15437_gb300 import engine as E
+    name = "separation_context_pairs.tsv"
+    _need(name)
+    pairs = W.separation_pairs(4)
+    hv = G.header_values(name)
+    assert hv["pairs_sha256"] == hashlib.sha256("\n".join(a + "\t" + b for a, b in pairs).encode()).hexdigest()
+    assert int(hv["sampled_range"]) == E.SEPARATION_SEARCH["frames_per_n"]
+    rows = [r for r in G.rows(name)]
+    assert rows
+    idx = [int(r[0]) for r in rows]
+    job = E.SeparateJob([pairs[i] for i in idx], **E.SEPARATION_SEARCH)
+    keys = [int(k) for k in job.run()]
+    for (i, n6, n7, n8, _), key in zip(rows, keys):
+        if n6 != "-":
+            f, v, w = (int(x) for x in n6.split(","))
+            want = mk.split_key(False, 6, f, v, w)
+        elif n7 != "-":
+            f, v, w = (int(x) for x in n7.split(","))
+            want = mk.split_key(True, 7, f, v, w)
+        elif n8 != "-":
+            f, v, w = (int(x) for x in n8.split(","))
+            want = mk.split_key(True, 8, f, v, w)
+        else:
+            want = mk.NO_KEY
+        assert key == want, (i, pairs[int(i)])
